@@ -1,0 +1,302 @@
+"""Benchmark of the three-species KLB hot path on GB300.
+
+Workload: the D3Q19 FP32 nanotube (512 x 128 x 128 box, staircase pipe of
+radius 48, 6-cell solid shell, seeded couplings).  One benchmark step is one
+check interval of the solver: 100 fused lattice steps (stream + collide +
+interface coupling of water, electrons and phonons) followed by the FP64
+observation pass (flow rate, slip length, masses, momenta, residual).
+
+Metric: MLUPS = active lattice sites (fluid + solid cells) updated per
+second, whole job.  With N GPUs (torchrun) every rank runs its own replica
+(independent channels of a design sweep: weak scaling, no data exchange).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LATTICE_STEPS_PER_STEP = 100
+PROFILE = os.path.join(ROOT, "profiles", "k_lattice_step_d3q19_fp32_nanotube_512x128x128.md")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("klb_kernels.cu", "klb_internal.h"):
+        with open(os.path.join(ROOT, "paper_2403_15768_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_hash and m_b) or m_hash.group(1) != _kernel_source_hash():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist_setup(gpus):
+    import torch
+    if gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        rank = int(os.environ.get("RANK", 0))
+        local = int(os.environ.get("LOCAL_RANK", 0))
+        world = int(os.environ.get("WORLD_SIZE", 1))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return rank, local, world, dist
+    return 0, 0, 1, None
+
+
+def _cpu_baseline(w, seconds=12.0):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload:
+    the full nanotube cross-section with 8 x planes (the geometry is
+    x-invariant, so the per-site work is that of the full box)."""
+    from oracle import Oracle, cross_section
+
+    nx = 8
+    geo = cross_section("pipe", w.ny, w.nz, radius=w.radius, shell=w.shell)
+    o = Oracle(19, nx, geo, tau=w.tau, rho0=w.rho0, G=w.G, couplings=w.couplings)
+    o.init_equilibrium()
+    sites = int(((geo.cs_type == 1) | (geo.cs_type == 2)).sum()) * nx
+    o.step(2)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(5)
+        n += 5
+    dt = time.perf_counter() - t0
+    return {"value": sites * n / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"nanotube cross-section 128x128 (r=48, shell 6) with nx={nx}, {n} FP64 "
+                      f"oracle steps in {dt:.1f} s, single thread"}
+
+
+def run_reference(args):
+    """The CPU oracle timed as the reference arm: each step is 10 oracle
+    lattice steps on the bounded sample (nanotube cross-section, nx = 8)."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    from oracle import Oracle, cross_section
+    from paper_2403_15768_gb300 import inputs
+
+    w = inputs.PIPE_D3Q19_FP32
+    nx = 8
+    geo = cross_section("pipe", w.ny, w.nz, radius=w.radius, shell=w.shell)
+    o = Oracle(19, nx, geo, tau=w.tau, rho0=w.rho0, G=w.G, couplings=w.couplings)
+    o.init_equilibrium()
+    sites = int(((geo.cs_type == 1) | (geo.cs_type == 2)).sum()) * nx
+    per = 10
+    for _ in range(args.warmup):
+        o.step(per)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(per)
+    dt = time.perf_counter() - t0
+    v = sites * per * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "sample_nx": nx, "lattice_steps_per_step": per},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"nanotube cross-section with nx={nx}, {per} steps per step"},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run(args):
+    import torch
+
+    from paper_2403_15768_gb300 import inputs, klb
+
+    rank, local, world, dist = _dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = inputs.PIPE_D3Q19_FP32
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        lat = klb.lattice_from_workload(w, device=dev, stream=stream)
+    sites = lat.active_sites()
+    species_cells = sum(lat.species_cells(s) for s in range(3))
+    bytes_per_launch = species_cells * 2 * 19 * 4  # read + write of every population, FP32
+
+    def interval():
+        lat.step(LATTICE_STEPS_PER_STEP)
+        return lat.observables()
+
+    for _ in range(args.warmup):
+        interval()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-timed region: inputs resident in HBM
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            lat.step(LATTICE_STEPS_PER_STEP)
+            ev[k][1].record(stream)
+            obs = lat.observables()
+        t_end.record(stream)
+        barrier()
+    ms = t_start.elapsed_time(t_end)
+    step_kernel_ms = sum(a.elapsed_time(b) for a, b in ev) / (args.steps * LATTICE_STEPS_PER_STEP)
+
+    # ---- end to end through the C ABI: couplings from pinned host memory,
+    # 100 steps, observables back to the host, every step.
+    cp_host = torch.tensor(w.couplings, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lat.set_couplings(*cp_host.tolist())
+        lat.step(LATTICE_STEPS_PER_STEP)
+        obs_e2e = lat.observables()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+
+    if dist is not None:
+        t = torch.tensor([ms, e2e_s * 1e3], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    else:
+        e2e_ms = e2e_s * 1e3
+
+    if rank != 0:
+        return
+    lattice_updates = sites * LATTICE_STEPS_PER_STEP * args.steps * world
+    value = lattice_updates / (ms * 1e-3) / 1e6
+    e2e_value = lattice_updates / (e2e_ms * 1e-3) / 1e6
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / (step_kernel_ms * 1e-3) / 1e9
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "lattice": "D3Q19", "box": [w.nx, w.ny, w.nz],
+                   "radius": w.radius, "shell": w.shell, "active_sites": sites,
+                   "species_cells": species_cells,
+                   "lattice_steps_per_step": LATTICE_STEPS_PER_STEP,
+                   "observables_per_step": 1, "parallelism": f"replicas x{world}",
+                   "l2": "working set 1.73 GB per GPU > 129 MB L2, no flush needed",
+                   "couplings": list(w.couplings)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": _ncu_traffic(),
+                     "kernel": "k_lattice<19,float,step>", "peak_source": peak_kind,
+                     "bytes_per_launch": bytes_per_launch, "launch_ms": step_kernel_ms},
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 40,
+                "d2h_bytes_per_step": 144},
+        "gpu_launches": args.steps * (LATTICE_STEPS_PER_STEP + 2),
+        "clocks": clk.summary(),
+        "observables": {"flow_rate": obs["flow_rate"], "slip_length": obs["slip_length"],
+                        "step": obs["step"], "e2e_step": obs_e2e["step"]},
+    }
+    if world == 1:
+        line["cpu_baseline"] = _cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * klb.h -- C ABI of the GB300 library for the three-species Keldysh-lattice
+ * Boltzmann (KLB) step: water ("hydron") populations in a nanochannel,
+ * electron and phonon populations in its solid walls (Sec. 4 of Succi &
+ * Montessori, "Keldysh-Lattice Boltzmann approach to quantum nanofluidics").
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * - Plain C types only.  Device memory is passed as void* (any cudaMalloc'd or
+ *   torch-allocated buffer on the current device); host arrays as plain
+ *   pointers.  The caller owns every buffer it passes; the library owns only
+ *   the handle and small host tables, and never calls cudaMalloc/cudaFree.
+ * - Errors are returned as klb_status; nothing is thrown across the ABI.
+ *   klb_last_error() gives the message of the last failing call on a handle.
+ * - One handle is used by one host thread at a time.  Work is enqueued on the
+ *   handle's CUDA stream; only calls documented as synchronising wait for it.
+ * - Dense host arrays ("box layout") index cell (x, y, z) as
+ *   x + nx * (y + ny * z), x fastest.  Arrays with a leading species index
+ *   use the order water (0), electron (1), phonon (2); arrays with a
+ *   component index use x, y, z.  Entries of cells that do not carry a
+ *   species are written as 0 and ignored on input.
+ * - Populations are deviations g_i = f_i - w_i rho0 from the rest state, in
+ *   the direction order: D2Q9 as numbered in Sec. 4.2 (0 rest, 1 right,
+ *   2 up, 3 left, 4 down, 5 right-up, 6 left-up, 7 left-down, 8 right-down);
+ *   D3Q19: 0 rest, (+x,-x,+y,-y,+z,-z), then (1,1,0), (-1,-1,0), (1,-1,0),
+ *   (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1),
+ *   (0,1,-1), (0,-1,1).
+ */
+#ifndef KLB_H
+#define KLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct klb_lattice klb_lattice; /* opaque, library-owned host handle */
+
+typedef enum {
+    KLB_OK = 0,
+    KLB_EINVAL = 1,    /* bad argument, shape, parameter or buffer size      */
+    KLB_ENOMEM = 2,    /* caller buffer too small, or host allocation failed */
+    KLB_ECUDA = 3,     /* a CUDA call failed (message in klb_last_error)      */
+    KLB_EUNSTABLE = 4, /* a non-finite value was seen                         */
+    KLB_ETIMEOUT = 5,  /* reserved for step/time limits of callers            */
+    KLB_ESTATE = 6     /* call not valid in the handle's current state        */
+} klb_status;
+
+enum { KLB_D2Q9 = 9, KLB_D3Q19 = 19 };
+enum { KLB_GEOM_SLAB = 0, KLB_GEOM_PIPE = 1, KLB_GEOM_MASK = 2 };
+enum { KLB_FP64 = 0, KLB_FP32 = 1 };
+enum { KLB_IFACE_SPECULAR = 0, KLB_IFACE_BOUNCEBACK = 1 };
+enum { KLB_WATER = 0, KLB_ELECTRON = 1, KLB_PHONON = 2 };
+
+/*
+ * Problem description (Sec. 2 set-up: water driven by a pressure gradient
+ * through a nanochannel with solid walls; x is the channel axis and is
+ * periodic, Sec. 4.2).
+ *   kind    KLB_D2Q9 (requires nz == 1) or KLB_D3Q19.
+ *   geom    SLAB: `width` fluid rows centred in y, `shell` solid rows on each
+ *           side, void beyond; walls normal to y; periodic in z.
+ *           PIPE: axis at (ny/2, nz/2); a cell centre (y+1/2, z+1/2) at
+ *           distance r is fluid if r < radius, solid if radius <= r <
+ *           radius + shell, void otherwise.
+ *           MASK: `mask` gives the cross-section (host, ny*nz bytes, index
+ *           y + ny*z; 0 void, 1 fluid, 2 solid), copied at creation;
+ *           periodic_y / periodic_z select periodic cross-section axes.
+ *   tau_*   BGK relaxation times of water, electrons, phonons (> 1/2).
+ *   rho0    rest density of every species (> 0).
+ *   G       uniform body-force density on the water: the pressure drive of
+ *           Eq. 2, applied with Guo forcing.
+ *   storage KLB_FP64 or KLB_FP32 populations; arithmetic in the same type.
+ *   iface_bc  KLB_IFACE_SPECULAR (free slip at the liquid/solid interface
+ *           for all species, Sec. 4.2) or KLB_IFACE_BOUNCEBACK (the Sec. 4.2
+ *           alternative); outer solid faces always bounce back.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t nx, ny, nz;
+    int32_t geom;
+    int32_t width;  /* SLAB */
+    int32_t radius; /* PIPE */
+    int32_t shell;  /* SLAB, PIPE */
+    int32_t periodic_y, periodic_z; /* MASK */
+    const uint8_t *mask;            /* MASK */
+    double tau_w, tau_e, tau_p;
+    double rho0;
+    double G[3];
+    int32_t storage;
+    int32_t iface_bc;
+} klb_desc;
+
+/*
+ * Friction coefficients (Eq. 27: F_kl = -F_lk = gamma_kl (u_k - u_l)), as
+ * force densities per unit velocity difference, symmetric in k, l:
+ *   g_we, g_wp  water-electron and water-phonon, per fluid/solid face
+ *               (Eq. 5, Eq. 11, Eq. 15);
+ *   g_ep        electron-phonon, per solid cell (Eqs. 12, 15);
+ *   g_ec, g_pc  electron and phonon loss to the crystal (Eqs. 13, 16).
+ * Negative values (negative quantum friction, Sec. 2) are accepted within the
+ * stability bound checked by klb_set_couplings.
+ */
+typedef struct {
+    double g_we, g_wp, g_ep, g_ec, g_pc;
+} klb_couplings;
+
+/*
+ * Observables of the current step n (after n completed steps): the
+ * velocities u(n) of the next step's moment pass.
+ *   flow_rate      (1/nx) * sum over fluid cells of u_x.
+ *   fit_A, fit_B   least squares u_x = A + B d^2 over fluid cells at distance
+ *                  d from the centre plane (slab) / axis (pipe) with
+ *                  d_wall - d >= 4; NaN for MASK geometries.
+ *   d_wall         slab: width/2; pipe: sqrt(fluid cells per slice / pi).
+ *   u_slip         A + B d_wall^2;  dudn_wall = |2 B d_wall|;
+ *   slip_length    u_slip / dudn_wall  (L_s = u_s / (du/dy)_w, Sec. 1).
+ *   u_wallrow_mean mean u_x over fluid cells with a solid face neighbour.
+ *   mean_u[s]      mean u_x of species s over its cells.
+ *   momentum[s]    sum of rho u_x;  mass[s] = sum of (rho - rho0).
+ *   residual       max over all species cells of |u_x(n) - u_x(n-1)|; NaN
+ *                  until two steps have run since creation, init or
+ *                  klb_set_state.
+ *   nonfinite      number of non-finite density/velocity values.
+ * All sums are accumulated in FP64 on the device.
+ */
+typedef struct {
+    int64_t step;
+    double flow_rate;
+    double fit_A, fit_B, d_wall;
+    double u_slip, dudn_wall, slip_length;
+    double u_wallrow_mean;
+    double mean_u[3];
+    double momentum[3];
+    double mass[3];
+    double residual;
+    int64_t nonfinite;
+} klb_obs;
+
+/* Device bytes klb_create_lattice needs for this description (0 if the
+ * description is invalid).  Pure host computation. */
+size_t klb_lattice_bytes(const klb_desc *desc);
+
+/* Sizes of a lattice, from the description alone (host computation):
+ *   fluid_cs / solid_cs     fluid / solid cells of one cross-section;
+ *   species_cells[s]        cells carrying species s (whole box);
+ *   active_sites            fluid + solid cells (whole box);
+ *   iface_cs[2]             fluid / solid cross-section cells with at least
+ *                           one fluid/solid face;
+ *   max_faces[2]            most such faces of one fluid / solid cell;
+ *   d_wall                  wall position of the slip fit (NaN for MASK);
+ *   bytes                   klb_lattice_bytes(desc). */
+typedef struct {
+    int64_t fluid_cs, solid_cs;
+    int64_t species_cells[3];
+    int64_t active_sites;
+    int64_t iface_cs[2];
+    int32_t max_faces[2];
+    double d_wall;
+    uint64_t bytes;
+} klb_info;
+
+/* Fill *info for a description; KLB_EINVAL (message via
+ * klb_last_error(NULL)) if it is invalid. */
+klb_status klb_lattice_info(const klb_desc *desc, klb_info *info);
+
+/*
+ * Build the lattice in the caller's device buffer `dev_buf` (at least
+ * klb_lattice_bytes(desc) bytes, 256-byte aligned, on the current device)
+ * and start from rest: every population deviation and lagged velocity is 0.
+ * `cuda_stream` is a cudaStream_t (NULL: the legacy default stream) on which
+ * all later work of the handle is enqueued.  `dev_buf` must outlive the
+ * handle.  Synchronises the stream once.  Returns KLB_EINVAL for a bad
+ * description (tau <= 1/2, rho0 <= 0, non-finite values, nz != 1 for D2Q9, a
+ * shell of 0, an empty species, a box too large for 32-bit row offsets),
+ * KLB_ENOMEM if `bytes` is too small.  Couplings start at zero.
+ */
+klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
+                              void *cuda_stream, klb_lattice **out);
+
+/* Set the friction coefficients.  KLB_EINVAL for non-finite values or for
+ * couplings beyond the stability bound of the lagged interface exchange:
+ * max over cells of (sum over its faces of |g| of its species pairs) must be
+ * below 0.6 rho0 (the exchange is stable for a pair relaxation rate below
+ * 4/3; see the design notes).  Host only; takes effect at the next step. */
+klb_status klb_set_couplings(klb_lattice *lat, const klb_couplings *c);
+
+/* Start from the local equilibrium of host fields in box layout:
+ * drho[3][ncell] density deviations and u[3][3][ncell] velocities (either
+ * may be NULL for zero).  The lagged interface velocities are set to u.
+ * Resets the step counter to 0.  Synchronises the stream. */
+klb_status klb_init_equilibrium(klb_lattice *lat, const double *drho, const double *u);
+
+/* Advance nsteps >= 0 lattice steps (stream + collide + interface coupling of
+ * all three species, one fused kernel per step).  Asynchronous. */
+klb_status klb_step(klb_lattice *lat, int64_t nsteps);
+
+/* Compute the observables of the current step into *out (host).
+ * Synchronises the stream.  Returns KLB_EUNSTABLE (with *out filled) when a
+ * non-finite value was seen. */
+klb_status klb_observables(klb_lattice *lat, klb_obs *out);
+
+/* Density deviations drho[3][ncell] and velocities u[3][3][ncell] of the
+ * current step, host, box layout (either may be NULL).  Synchronises. */
+klb_status klb_get_field(klb_lattice *lat, double *drho, double *u);
+
+/* Current state to host, box layout: post-collision deviations
+ * g[3][Q][ncell] and the velocities of the two previous steps
+ * U1[3][3][ncell] = u(n-1), U2 = u(n-2).  The lagged velocities are kept
+ * only at interface cells; other cells read 0.  Any pointer may be NULL.
+ * Synchronises. */
+klb_status klb_get_state(klb_lattice *lat, double *g, double *U1, double *U2);
+
+/* Replace the state (same layouts as klb_get_state; U1/U2 are read at
+ * interface cells only) and set the step counter.  Synchronises. */
+klb_status klb_set_state(klb_lattice *lat, const double *g, const double *U1,
+                         const double *U2, int64_t step);
+
+/* Number of completed steps, lattice sizes and species-cell counts. */
+int64_t klb_get_step(const klb_lattice *lat);
+int64_t klb_species_cells(const klb_lattice *lat, int species);
+
+/* Release the handle (not the caller's buffer).  Synchronises. */
+klb_status klb_destroy(klb_lattice *lat);
+
+/* Message of the last failing call on `lat` ("" if none); a message for
+ * failures that produced no handle when `lat` is NULL.  Valid until the next
+ * call on the same handle. */
+const char *klb_last_error(const klb_lattice *lat);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KLB_H */

@@ -1,0 +1,121 @@
+// Internal declarations of the KLB library: host geometry tables, device
+// memory plan and kernel launchers.  Not part of the public ABI (include/klb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "klb.h"
+
+namespace klb {
+
+constexpr int kMaxFaces = 4;   // fluid/solid faces of one cross-section cell (+-y, +-z)
+constexpr int kBlockX = 128;   // threads per block along x (one x per thread)
+
+// Row classes: a row is one cross-section cell together with all its x.
+// Water lives on fluid rows; electrons and phonons share the solid rows.
+enum RowClass { kFluid = 0, kSolid = 1 };
+
+// Per-row table, read once per block (all threads of a block share a row).
+struct RowInfo {
+    int32_t src[19];            // element offset (dir' * n_rows + row') * nxp of the
+                                // row that direction i is pulled from
+    uint32_t xm;                // bit i: pull direction i from x - 1
+    uint32_t xp;                // bit i: pull direction i from x + 1
+    int32_t slot;               // interface slot of this row, -1 if none
+    int32_t nface;              // number of fluid/solid faces
+    int32_t partner[kMaxFaces]; // interface slots of the rows across those faces
+    float d2;                   // fluid rows: squared distance to centre plane / axis
+    int32_t flags;              // fluid rows: bit 0 in the slip fit, bit 1 wall row
+    int32_t pad[3];
+};
+static_assert(sizeof(RowInfo) == 128, "RowInfo is one 128-byte line");
+
+enum RowFlags { kFitRow = 1, kWallRow = 2 };
+
+// Indices of the FP64 partial sums reduced by the observation kernel.
+enum SumIndex {
+    kSumUxFluid = 0,   // sum of u_x over fluid cells
+    kSumFitN,          // slip fit: count, sum d^2, sum d^4, sum u, sum u d^2
+    kSumFitD2,
+    kSumFitD4,
+    kSumFitU,
+    kSumFitUD2,
+    kSumWallN,         // wall-row count and sum u_x
+    kSumWallU,
+    kSumUxE,           // electron / phonon sum u_x
+    kSumUxP,
+    kSumMomW,          // sum rho u_x per species
+    kSumMomE,
+    kSumMomP,
+    kSumMassW,         // sum (rho - rho0) per species
+    kSumMassE,
+    kSumMassP,
+    kSumNonfinite,     // count of non-finite rho/u values
+    kSumResidual,      // max |u_x(n) - u_x(n-1)| (a max, not a sum)
+    kNumSums
+};
+
+// Host geometry of one lattice (built from the description only).
+struct Geometry {
+    int Q = 0, nx = 0, ny = 0, nz = 0, nxp = 0;
+    int periodic_y = 0, periodic_z = 0;
+    std::vector<uint8_t> cs_type;          // ny*nz, index y + ny*z
+    std::vector<int> rows[2];              // cross-section index of each row
+    std::vector<int> row_of_cs[2];         // row of a cross-section cell, -1 if none
+    std::vector<RowInfo> info[2];
+    std::vector<int> slot_row[2];          // row of each interface slot
+    int max_faces[2] = {0, 0};
+    double d_wall = 0.0;
+    bool has_fit = false;
+};
+
+// Builds the geometry and its streaming / interface tables.  Returns false
+// with a message on an invalid description.
+bool build_geometry(const klb_desc &d, Geometry &g, std::string &err);
+
+// Offsets (bytes from the caller's buffer) of every device region.
+struct MemoryPlan {
+    size_t pop[2][3];      // [buffer][species]
+    size_t pop_bytes[3];
+    size_t U[3][2];        // [time slot][row class]
+    size_t U_bytes[2];
+    size_t rows[2];
+    size_t partials, sums, field;
+    size_t field_bytes;
+    size_t total;
+    int nblocks_w, nblocks_s, nchunk, bx;
+};
+MemoryPlan plan_memory(const Geometry &g, int storage);
+
+// Kernel arguments.  T is the storage and arithmetic type (float or double).
+template <typename T>
+struct StepArgs {
+    const T *in[3];        // current state, per species
+    T *out[3];             // next state (step mode)
+    const T *in_prev[3];   // previous state (observe mode, residual)
+    const RowInfo *rows[2];
+    const T *U1[2], *U2[2], *U3[2];  // lagged velocities u(n-1), u(n-2), u(n-3)
+    T *U0[2];                        // u(n) written here (step mode)
+    int nx, nxp, nchunk, nbw;
+    int n_rows[2], n_slots[2];
+    T rho0, om[3], G[3];
+    T g_we, g_wp, g_ep, g_ec, g_pc;
+    double *partials;      // observe mode: [block][kNumSums]
+    int residual_valid;
+    T *field;              // field / init mode: per species [4][n_rows][nxp]
+};
+
+enum Mode { kModeStep = 0, kModeObserve = 1, kModeField = 2 };
+
+// Launchers (return the launch error, if any).
+cudaError_t launch_step(int Q, int storage, const void *args, int mode, int nblocks, int bx,
+                        cudaStream_t s);
+cudaError_t launch_init(int Q, int storage, const void *args, int nblocks, int bx,
+                        cudaStream_t s);
+cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s);
+
+}  // namespace klb

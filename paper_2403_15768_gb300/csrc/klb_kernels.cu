@@ -1,0 +1,533 @@
+// CUDA kernels of the KLB step for sm_103a.
+//
+// One fused kernel per lattice step updates all three species (Sec. 4: one
+// population set per species, {h_i, e_i, p_i}):
+//   pull-stream (boundary rules of Sec. 4.2, precomputed per row) ->
+//   moments -> interface friction (Eq. 27) from lagged velocities ->
+//   trapezoidal electron-phonon friction and crystal sinks (Eqs. 12, 13, 16) ->
+//   Guo velocity -> BGK collision with Guo forcing (body force of Eq. 2) ->
+//   store (A-B: the state is read from one buffer and written to the other).
+//
+// Layout: structure of arrays, per species [direction][row][x] with rows of
+// nxp elements (x fastest, rows padded to 32 elements), so every load and
+// store of a warp is a contiguous run of x.  A block covers up to 128
+// consecutive x of one row: the row table (sources, x shifts, interface
+// partners) is block-uniform.  Water blocks come first in the grid, then the
+// solid blocks, each of which updates the electrons and phonons of its row.
+//
+// The same per-cell code serves three modes: the step, the observation pass
+// (velocities of the current and previous step reduced in FP64, no stores of
+// populations) and the field pass (velocities written to a scratch field).
+
+#include <cuda_runtime.h>
+
+#include "klb_internal.h"
+
+namespace klb {
+
+// ---------------------------------------------------------------------------
+// Lattice constants, folded at compile time inside unrolled loops.
+
+template <int Q> __host__ __device__ constexpr int cx(int i);
+template <int Q> __host__ __device__ constexpr int cy(int i);
+template <int Q> __host__ __device__ constexpr int cz(int i);
+template <int Q> __host__ __device__ constexpr double wt(int i);
+
+template <> __host__ __device__ constexpr int cx<9>(int i)
+{
+    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+template <> __host__ __device__ constexpr int cy<9>(int i)
+{
+    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+template <> __host__ __device__ constexpr int cz<9>(int) { return 0; }
+template <> __host__ __device__ constexpr double wt<9>(int i)
+{
+    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// D3Q19: 0 rest; 1..6 (+x,-x,+y,-y,+z,-z); 7..18 edges in opposite pairs.
+__host__ __device__ constexpr int c19(int i, int a)
+{
+    constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                              {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                              {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                              {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return t[i][a];
+}
+template <> __host__ __device__ constexpr int cx<19>(int i) { return c19(i, 0); }
+template <> __host__ __device__ constexpr int cy<19>(int i) { return c19(i, 1); }
+template <> __host__ __device__ constexpr int cz<19>(int i) { return c19(i, 2); }
+template <> __host__ __device__ constexpr double wt<19>(int i)
+{
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct Cell {
+    T drho;   // density deviation
+    T u[3];   // Guo velocity (j + F/2) / rho
+    T F[3];   // total force density
+};
+
+// Pull-stream the Q populations of one species at (row, x).
+template <int Q, typename T>
+__device__ __forceinline__ void pull(const T *__restrict__ in, const RowInfo &R, int x, int xm1,
+                                     int xp1, T g[Q])
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int xs = ((R.xm >> i) & 1u) ? xm1 : (((R.xp >> i) & 1u) ? xp1 : x);
+        g[i] = __ldg(in + R.src[i] + xs);
+    }
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void moments(const T g[Q], T &drho, T j[3])
+{
+    drho = T(0);
+    j[0] = j[1] = j[2] = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += g[i];
+        if (cx<Q>(i) > 0) j[0] += g[i];
+        if (cx<Q>(i) < 0) j[0] -= g[i];
+        if (cy<Q>(i) > 0) j[1] += g[i];
+        if (cy<Q>(i) < 0) j[1] -= g[i];
+        if (cz<Q>(i) > 0) j[2] += g[i];
+        if (cz<Q>(i) < 0) j[2] -= g[i];
+    }
+}
+
+// Index of the direction with velocity (a, b, c), at compile time.
+template <int Q>
+__host__ __device__ constexpr int dir_index(int a, int b, int c)
+{
+    int k = -1;
+    for (int i = 0; i < Q; ++i)
+        if (cx<Q>(i) == a && cy<Q>(i) == b && cz<Q>(i) == c) k = i;
+    return k;
+}
+
+// BGK with Guo forcing, deviation form:
+// g*_i = g_i + om (geq_i - g_i) + (1 - om/2) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F,
+// geq_i = w_i [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)].
+// The exact scheme conserves mass and gives post-collision momentum j + F.
+// In FP32 the lattice weights (1/18, 1/36, ...) are not representable, and
+// the rounded weights bias both moments by the same relative amount in every
+// cell and every step, a drift that accumulates over the slow relaxation of
+// the channel flow.  FP32 therefore restores the two moments after the
+// collision: the mass residual goes to the rest population, the momentum
+// residual of each axis to its pair of axis populations.  The remaining
+// rounding is unbiased.
+template <int Q, typename T>
+__device__ __forceinline__ void collide_store(T g[Q], const Cell<T> &c, const T j[3], T rho0,
+                                              T om, T *__restrict__ out, int row_stride, int base)
+{
+    const T rho = rho0 + c.drho;
+    const T uu = c.u[0] * c.u[0] + c.u[1] * c.u[1] + c.u[2] * c.u[2];
+    const T uF = c.u[0] * c.F[0] + c.u[1] * c.F[1] + c.u[2] * c.F[2];
+    const T e0 = c.drho - T(1.5) * rho * uu;
+    const T r3 = T(3) * rho, r45 = T(4.5) * rho;
+    const T m3uF = T(-3) * uF;
+    const T om1 = T(1) - om;
+    const T fo = T(1) - T(0.5) * om;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T w = T(wt<Q>(i));
+        T cu = T(0), cF = T(0);
+        if (cx<Q>(i)) { cu += T(cx<Q>(i)) * c.u[0]; cF += T(cx<Q>(i)) * c.F[0]; }
+        if (cy<Q>(i)) { cu += T(cy<Q>(i)) * c.u[1]; cF += T(cy<Q>(i)) * c.F[1]; }
+        if (cz<Q>(i)) { cu += T(cz<Q>(i)) * c.u[2]; cF += T(cz<Q>(i)) * c.F[2]; }
+        const T teq = e0 + cu * (r3 + r45 * cu);
+        const T tF = m3uF + cF * (T(3) + T(9) * cu);
+        g[i] = om1 * g[i] + (om * w) * teq + (fo * w) * tF;
+    }
+    if (sizeof(T) == 4) {
+        T m = T(0), p[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            m += g[i];
+            if (cx<Q>(i)) p[0] += T(cx<Q>(i)) * g[i];
+            if (cy<Q>(i)) p[1] += T(cy<Q>(i)) * g[i];
+            if (cz<Q>(i)) p[2] += T(cz<Q>(i)) * g[i];
+        }
+        g[0] += c.drho - m;
+        const T hx = T(0.5) * ((j[0] + c.F[0]) - p[0]);
+        const T hy = T(0.5) * ((j[1] + c.F[1]) - p[1]);
+        g[dir_index<Q>(1, 0, 0)] += hx;
+        g[dir_index<Q>(-1, 0, 0)] -= hx;
+        g[dir_index<Q>(0, 1, 0)] += hy;
+        g[dir_index<Q>(0, -1, 0)] -= hy;
+        if (Q == 19) {
+            const T hz = T(0.5) * ((j[2] + c.F[2]) - p[2]);
+            g[dir_index<Q>(0, 0, 1)] += hz;
+            g[dir_index<Q>(0, 0, -1)] -= hz;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i * row_stride + base] = g[i];
+}
+
+template <typename T>
+__device__ __forceinline__ T lagged(const T *U1, const T *U2, int idx)
+{
+    return T(0.5) * (U1[idx] + U2[idx]);
+}
+
+// Water cell: moments, interface friction, Guo velocity.  U1/U2 are the
+// velocities of the two previous steps of the same time level as `in`.
+template <int Q, typename T>
+__device__ __forceinline__ void water_cell(const StepArgs<T> &p, const T *__restrict__ in,
+                                           const T *Uw1, const T *Uw2, const T *Us1,
+                                           const T *Us2, const RowInfo &R, int x, int xm1,
+                                           int xp1, T g[Q], Cell<T> &c, T j[3])
+{
+    pull<Q, T>(in, R, x, xm1, xp1, g);
+    moments<Q, T>(g, c.drho, j);
+    c.F[0] = p.G[0];
+    c.F[1] = p.G[1];
+    c.F[2] = p.G[2];
+    if (R.slot >= 0) {
+        const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
+        for (int a = 0; a < 3; ++a) {
+            const T uw = lagged(Uw1, Uw2, (a * ns_w + R.slot) * nxp + x);
+            T f = T(0);
+            for (int k = 0; k < R.nface; ++k) {
+                const int q = R.partner[k];
+                const T de = uw - lagged(Us1, Us2, (a * ns_s + q) * nxp + x);
+                const T dp = uw - lagged(Us1, Us2, ((a + 3) * ns_s + q) * nxp + x);
+                f -= p.g_we * de + p.g_wp * dp;
+            }
+            c.F[a] += f;
+        }
+    }
+    const T rinv = T(1) / (p.rho0 + c.drho);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c.u[a] = (j[a] + T(0.5) * c.F[a]) * rinv;
+}
+
+// Solid cell: electrons and phonons of one cell.
+template <int Q, typename T>
+__device__ __forceinline__ void solid_cell(const StepArgs<T> &p, const T *__restrict__ in_e,
+                                           const T *__restrict__ in_p, const T *Uw1,
+                                           const T *Uw2, const T *Us1, const T *Us2,
+                                           const RowInfo &R, int x, int xm1, int xp1, T ge[Q],
+                                           T gp[Q], Cell<T> &ce, Cell<T> &cp, T je[3], T jp[3])
+{
+    pull<Q, T>(in_e, R, x, xm1, xp1, ge);
+    pull<Q, T>(in_p, R, x, xm1, xp1, gp);
+    moments<Q, T>(ge, ce.drho, je);
+    moments<Q, T>(gp, cp.drho, jp);
+    T Fe[3] = {T(0), T(0), T(0)}, Fp[3] = {T(0), T(0), T(0)};
+    if (R.slot >= 0) {
+        const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
+        for (int a = 0; a < 3; ++a) {
+            const T ue = lagged(Us1, Us2, (a * ns_s + R.slot) * nxp + x);
+            const T up = lagged(Us1, Us2, ((a + 3) * ns_s + R.slot) * nxp + x);
+            T fe = T(0), fp = T(0);
+            for (int k = 0; k < R.nface; ++k) {
+                const T uw = lagged(Uw1, Uw2, (a * ns_w + R.partner[k]) * nxp + x);
+                fe += p.g_we * (uw - ue);
+                fp += p.g_wp * (uw - up);
+            }
+            Fe[a] = fe;
+            Fp[a] = fp;
+        }
+    }
+    // Trapezoidal e-p friction and sinks, solved exactly per component:
+    // (a + k + se) ue - k up = Je,  -k ue + (b + k + sp) up = Jp.
+    const T ra = p.rho0 + ce.drho, rb = p.rho0 + cp.drho;
+    const T k = T(0.5) * p.g_ep, se = T(0.5) * p.g_ec, sp = T(0.5) * p.g_pc;
+    const T A = ra + k + se, B = rb + k + sp;
+    const T Dinv = T(1) / (A * B - k * k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T Je = je[a] + T(0.5) * Fe[a];
+        const T Jp = jp[a] + T(0.5) * Fp[a];
+        const T ue = (B * Je + k * Jp) * Dinv;
+        const T up = (A * Jp + k * Je) * Dinv;
+        ce.u[a] = ue;
+        cp.u[a] = up;
+        ce.F[a] = Fe[a] - p.g_ep * (ue - up) - p.g_ec * ue;
+        cp.F[a] = Fp[a] + p.g_ep * (ue - up) - p.g_pc * up;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of the observation sums (FP64, fixed order).
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ void block_reduce_store(double (&s)[kNumSums], double *out)
+{
+    __shared__ double red[kNumSums][kBlockX / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < kNumSums; ++k) {
+        double v = (k == kSumResidual) ? warp_max(s[k]) : warp_sum(s[k]);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumSums) {
+        const int k = threadIdx.x;
+        double v = red[k][0];
+        for (int w = 1; w < nwarps; ++w) v = (k == kSumResidual) ? fmax(v, red[k][w]) : v + red[k][w];
+        out[k] = v;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ bool finite3(const Cell<T> &c)
+{
+    return isfinite((double)c.drho) && isfinite((double)c.u[0]) && isfinite((double)c.u[1]) &&
+           isfinite((double)c.u[2]);
+}
+
+// ---------------------------------------------------------------------------
+
+template <int Q, typename T, int MODE>
+__global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
+{
+    const int b = blockIdx.x;
+    const bool water = b < p.nbw;
+    const int bb = water ? b : b - p.nbw;
+    const int row = bb / p.nchunk;
+    const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
+    const bool live = x < p.nx;
+
+    double s[kNumSums];
+    if (MODE == kModeObserve) {
+#pragma unroll
+        for (int k = 0; k < kNumSums; ++k) s[k] = 0.0;
+    }
+
+    if (live) {
+        const int xm1 = x == 0 ? p.nx - 1 : x - 1;
+        const int xp1 = x == p.nx - 1 ? 0 : x + 1;
+        const int nxp = p.nxp;
+        if (water) {
+            const RowInfo &R = p.rows[kFluid][row];
+            const int stride = p.n_rows[kFluid] * nxp, base = row * nxp + x;
+            T g[Q], j[3];
+            Cell<T> c;
+            water_cell<Q, T>(p, p.in[0], p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R,
+                             x, xm1, xp1, g, c, j);
+            if (MODE == kModeStep) {
+                if (R.slot >= 0) {
+                    const int ns = p.n_slots[kFluid];
+                    for (int a = 0; a < 3; ++a) p.U0[kFluid][(a * ns + R.slot) * nxp + x] = c.u[a];
+                }
+                collide_store<Q, T>(g, c, j, p.rho0, p.om[0], p.out[0], stride, base);
+            } else if (MODE == kModeField) {
+                T *f = p.field;
+                f[row * nxp + x] = c.drho;
+                for (int a = 0; a < 3; ++a) f[((a + 1) * p.n_rows[kFluid] + row) * nxp + x] = c.u[a];
+            } else {
+                const double ux = (double)c.u[0];
+                const double rho = (double)(p.rho0 + c.drho);
+                s[kSumUxFluid] = ux;
+                s[kSumMomW] = rho * ux;
+                s[kSumMassW] = (double)c.drho;
+                s[kSumNonfinite] = finite3(c) ? 0.0 : 1.0;
+                if (R.flags & kFitRow) {
+                    const double d2 = (double)R.d2;
+                    s[kSumFitN] = 1.0;
+                    s[kSumFitD2] = d2;
+                    s[kSumFitD4] = d2 * d2;
+                    s[kSumFitU] = ux;
+                    s[kSumFitUD2] = ux * d2;
+                }
+                if (R.flags & kWallRow) {
+                    s[kSumWallN] = 1.0;
+                    s[kSumWallU] = ux;
+                }
+                if (p.residual_valid) {
+                    Cell<T> cprev;
+                    water_cell<Q, T>(p, p.in_prev[0], p.U2[kFluid], p.U3[kFluid], p.U2[kSolid],
+                                     p.U3[kSolid], R, x, xm1, xp1, g, cprev, j);
+                    s[kSumResidual] = fabs(ux - (double)cprev.u[0]);
+                }
+            }
+        } else {
+            const RowInfo &R = p.rows[kSolid][row];
+            const int stride = p.n_rows[kSolid] * nxp, base = row * nxp + x;
+            T ge[Q], gp[Q], je[3], jp[3];
+            Cell<T> ce, cp;
+            solid_cell<Q, T>(p, p.in[1], p.in[2], p.U1[kFluid], p.U2[kFluid], p.U1[kSolid],
+                             p.U2[kSolid], R, x, xm1, xp1, ge, gp, ce, cp, je, jp);
+            if (MODE == kModeStep) {
+                if (R.slot >= 0) {
+                    const int ns = p.n_slots[kSolid];
+                    for (int a = 0; a < 3; ++a) {
+                        p.U0[kSolid][(a * ns + R.slot) * nxp + x] = ce.u[a];
+                        p.U0[kSolid][((a + 3) * ns + R.slot) * nxp + x] = cp.u[a];
+                    }
+                }
+                collide_store<Q, T>(ge, ce, je, p.rho0, p.om[1], p.out[1], stride, base);
+                collide_store<Q, T>(gp, cp, jp, p.rho0, p.om[2], p.out[2], stride, base);
+            } else if (MODE == kModeField) {
+                const int nrw = p.n_rows[kFluid], nrs = p.n_rows[kSolid];
+                T *fe = p.field + (size_t)4 * nrw * nxp;
+                T *fp = fe + (size_t)4 * nrs * nxp;
+                fe[(0 * nrs + row) * nxp + x] = ce.drho;
+                fp[(0 * nrs + row) * nxp + x] = cp.drho;
+                for (int a = 0; a < 3; ++a) {
+                    fe[((a + 1) * nrs + row) * nxp + x] = ce.u[a];
+                    fp[((a + 1) * nrs + row) * nxp + x] = cp.u[a];
+                }
+            } else {
+                const double ue = (double)ce.u[0], up = (double)cp.u[0];
+                s[kSumUxE] = ue;
+                s[kSumUxP] = up;
+                s[kSumMomE] = (double)(p.rho0 + ce.drho) * ue;
+                s[kSumMomP] = (double)(p.rho0 + cp.drho) * up;
+                s[kSumMassE] = (double)ce.drho;
+                s[kSumMassP] = (double)cp.drho;
+                s[kSumNonfinite] = (finite3(ce) ? 0.0 : 1.0) + (finite3(cp) ? 0.0 : 1.0);
+                if (p.residual_valid) {
+                    Cell<T> pe, pp;
+                    solid_cell<Q, T>(p, p.in_prev[1], p.in_prev[2], p.U2[kFluid], p.U3[kFluid],
+                                     p.U2[kSolid], p.U3[kSolid], R, x, xm1, xp1, ge, gp, pe, pp, je,
+                                     jp);
+                    s[kSumResidual] = fmax(fabs(ue - (double)pe.u[0]), fabs(up - (double)pp.u[0]));
+                }
+            }
+        }
+    }
+    if (MODE == kModeObserve) block_reduce_store(s, p.partials + (size_t)b * kNumSums);
+}
+
+// Start from the local equilibrium of the fields (drho, u) staged in p.field
+// (the layout the field pass writes): the state buffer p.out and the
+// lagged-velocity slot p.U0 are filled; the host copies them to the others.
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlockX) k_init(const StepArgs<T> p)
+{
+    const int b = blockIdx.x;
+    const bool water = b < p.nbw;
+    const int bb = water ? b : b - p.nbw;
+    const int row = bb / p.nchunk;
+    const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const int nxp = p.nxp;
+    const int nrw = p.n_rows[kFluid], nrs = p.n_rows[kSolid];
+    const int cls = water ? kFluid : kSolid;
+    const RowInfo &R = p.rows[cls][row];
+    const int nsp = water ? 1 : 2;
+    for (int k = 0; k < nsp; ++k) {
+        const int s = water ? 0 : 1 + k;
+        const int nr = water ? nrw : nrs;
+        const T *f = p.field;
+        if (s >= 1) f += (size_t)4 * nrw * nxp;
+        if (s == 2) f += (size_t)4 * nrs * nxp;
+        Cell<T> c;
+        c.drho = f[row * nxp + x];
+        for (int a = 0; a < 3; ++a) {
+            c.u[a] = f[((a + 1) * nr + row) * nxp + x];
+            c.F[a] = T(0);
+        }
+        // om = 1 and F = 0 make collide_store write exactly g^eq, whose
+        // moments are drho and rho u.
+        T g[Q], jeq[3];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = T(0);
+        for (int a = 0; a < 3; ++a) jeq[a] = (p.rho0 + c.drho) * c.u[a];
+        collide_store<Q, T>(g, c, jeq, p.rho0, T(1), p.out[s], nr * nxp, row * nxp + x);
+        if (R.slot >= 0) {
+            const int ns = p.n_slots[cls];
+            const int off = water ? 0 : 3 * k;
+            for (int a = 0; a < 3; ++a) p.U0[cls][((a + off) * ns + R.slot) * nxp + x] = c.u[a];
+        }
+    }
+}
+
+// Deterministic final reduction of the per-block partial sums (one block).
+__global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ partials, int nblocks,
+                                                  double *__restrict__ sums)
+{
+    __shared__ double red[256];
+    for (int k = 0; k < kNumSums; ++k) {
+        const bool is_max = k == kSumResidual;
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+            const double q = partials[(size_t)b * kNumSums + k];
+            v = is_max ? fmax(v, q) : v + q;
+        }
+        red[threadIdx.x] = v;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w)
+                red[threadIdx.x] = is_max ? fmax(red[threadIdx.x], red[threadIdx.x + w])
+                                          : red[threadIdx.x] + red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) sums[k] = red[0];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+
+template <int Q, typename T>
+static cudaError_t launch_step_t(const void *args, int mode, int nblocks, int bx, cudaStream_t s)
+{
+    const StepArgs<T> &a = *static_cast<const StepArgs<T> *>(args);
+    if (mode == kModeStep)
+        k_lattice<Q, T, kModeStep><<<nblocks, bx, 0, s>>>(a);
+    else if (mode == kModeObserve)
+        k_lattice<Q, T, kModeObserve><<<nblocks, bx, 0, s>>>(a);
+    else
+        k_lattice<Q, T, kModeField><<<nblocks, bx, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(int Q, int storage, const void *args, int mode, int nblocks, int bx,
+                        cudaStream_t s)
+{
+    if (Q == 9)
+        return storage == KLB_FP64 ? launch_step_t<9, double>(args, mode, nblocks, bx, s)
+                                   : launch_step_t<9, float>(args, mode, nblocks, bx, s);
+    return storage == KLB_FP64 ? launch_step_t<19, double>(args, mode, nblocks, bx, s)
+                               : launch_step_t<19, float>(args, mode, nblocks, bx, s);
+}
+
+cudaError_t launch_init(int Q, int storage, const void *args, int nblocks, int bx, cudaStream_t s)
+{
+    if (Q == 9) {
+        if (storage == KLB_FP64)
+            k_init<9, double><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<double> *>(args));
+        else
+            k_init<9, float><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<float> *>(args));
+    } else {
+        if (storage == KLB_FP64)
+            k_init<19, double><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<double> *>(args));
+        else
+            k_init<19, float><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<float> *>(args));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s)
+{
+    k_finalize<<<1, 256, 0, s>>>(partials, nblocks, sums);
+    return cudaGetLastError();
+}
+
+}  // namespace klb

@@ -1,0 +1,86 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+Holds none of the method's arithmetic: named workload presets (sizes and
+parameters of the nanochannel set-ups), the coupling draws and the random
+numbers of perturbed starts.  Both the CUDA path and the CPU oracle take
+these as inputs and compute everything else themselves.
+
+The paper runs no simulation and names no dataset; its set-ups (Sec. 2,
+Sec. 5.1: water driven through a carbon nanotube or a slab channel with
+solid walls carrying electrons and phonons) are stood in for by these
+synthetic channels.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    kind: int            # 9 (D2Q9) or 19 (D3Q19)
+    geom: str            # "slab", "pipe" or "mask"
+    nx: int
+    ny: int
+    nz: int
+    width: int = 0       # slab fluid rows
+    radius: int = 0      # pipe radius
+    shell: int = 0       # solid thickness
+    tau: tuple = (0.8, 0.6, 1.0)
+    rho0: float = 1.0
+    G: tuple = (1e-6, 0.0, 0.0)
+    couplings: tuple = (0.0, 0.0, 0.0, 0.0, 0.0)  # g_we, g_wp, g_ep, g_ec, g_pc
+    storage: str = "fp32"
+    steps: int = 0
+    iface_bc: str = "specular"
+    extra: dict = field(default_factory=dict)
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def draw_couplings(seed: int = 0):
+    """Four couplings log-uniform in [1e-3, 1e-1] from numpy's default_rng(seed),
+    in the order (g_we, g_wp, g_ep, g_pc); g_ec = 0."""
+    rng = np.random.default_rng(seed)
+    g_we, g_wp, g_ep, g_pc = 10 ** rng.uniform(-3, -1, 4)
+    return (float(g_we), float(g_wp), float(g_ep), 0.0, float(g_pc))
+
+
+# D2Q9 FP64 slab: periodic nx = 64, 32 fluid rows, 4 solid rows per wall.
+SLAB_D2Q9_FP64 = Workload(
+    name="d2q9_fp64_slab_64x40", kind=9, geom="slab", nx=64, ny=40, nz=1, width=32, shell=4,
+    tau=(0.8, 0.6, 1.0), G=(1e-6, 0.0, 0.0), couplings=(0.05, 0.02, 0.1, 0.0, 0.01),
+    storage="fp64", steps=10_000)
+
+# D3Q19 FP32 nanotube: 512 x 128 x 128 box, staircase pipe of radius 48 with a
+# 6-cell shell, couplings drawn from seed 0.
+PIPE_D3Q19_FP32 = Workload(
+    name="d3q19_fp32_pipe_512x128x128_r48", kind=19, geom="pipe", nx=512, ny=128, nz=128,
+    radius=48, shell=6, tau=(0.7, 0.6, 1.0), G=(1e-6, 0.0, 0.0), couplings=draw_couplings(0),
+    storage="fp32", steps=5_000)
+
+# Same nanotube scaled by 1.5 (radius 72, shell 9) and its 128 x 64 x 64
+# subcase (radius 24, shell 3).
+PIPE_D3Q19_LARGE = PIPE_D3Q19_FP32.with_(
+    name="d3q19_pipe_768x192x192_r72", nx=768, ny=192, nz=192, radius=72, shell=9)
+PIPE_D3Q19_SUB = PIPE_D3Q19_FP32.with_(
+    name="d3q19_pipe_128x64x64_r24", nx=128, ny=64, nz=64, radius=24, shell=3)
+
+PRESETS = {w.name: w for w in (SLAB_D2Q9_FP64, PIPE_D3Q19_FP32, PIPE_D3Q19_LARGE,
+                               PIPE_D3Q19_SUB)}
+
+
+def perturbation(w: Workload, seed: int, eps: float):
+    """Random numbers of a perturbed start: drho = rho0 * eps * xi and
+    u = eps * eta with xi, eta ~ U(-1, 1) from default_rng(seed), one draw
+    per species, component and cell, in box order (x fastest).  u_z = 0 on
+    D2Q9.  Shapes (3, nz, ny, nx) and (3, 3, nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    xi = rng.uniform(-1.0, 1.0, (3, w.nz, w.ny, w.nx))
+    eta = rng.uniform(-1.0, 1.0, (3, 3, w.nz, w.ny, w.nx))
+    if w.kind == 9:
+        eta[:, 2] = 0.0
+    return w.rho0 * eps * xi, eps * eta

@@ -1,0 +1,91 @@
+"""CPU tests of the C ABI library: it builds, loads without a GPU, exports
+every entry point declared in include/klb.h, and its host-side geometry
+(rows, interface cells, fit wall) agrees with the oracle's independent one."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from klb_testutil import oracle_geometry
+from oracle.oracle import _solid_face_count
+from paper_2403_15768_gb300 import inputs, klb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = klb.load_library()
+    with open(os.path.join(ROOT, "include", "klb.h")) as fh:
+        header = fh.read()
+    declared = set(re.findall(r"^\s*(?:klb_status|size_t|int64_t|const char \*)\s*\*?\s*(klb_\w+)\s*\(",
+                              header, re.M))
+    assert {"klb_create_lattice", "klb_step", "klb_observables", "klb_set_couplings"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(klb.EXPORTS)
+
+
+def _geometry_cases():
+    yield inputs.SLAB_D2Q9_FP64
+    yield inputs.PIPE_D3Q19_FP32
+    yield inputs.PIPE_D3Q19_LARGE
+    yield inputs.PIPE_D3Q19_SUB
+    yield inputs.PIPE_D3Q19_SUB.with_(name="odd", nx=37, ny=17, nz=15, radius=5, shell=2)
+    yield inputs.PIPE_D3Q19_SUB.with_(name="thin", nx=5, ny=12, nz=12, radius=3, shell=1)
+    yield inputs.SLAB_D2Q9_FP64.with_(name="slab3d", kind=19, nx=9, ny=14, nz=3, width=6, shell=3,
+                                      storage="fp32")
+
+
+@pytest.mark.parametrize("w", list(_geometry_cases()), ids=lambda w: w.name)
+def test_host_geometry_matches_oracle(w):
+    info = klb.klb_lattice_info(klb.desc_from_workload(w))
+    geo = oracle_geometry(w)
+    nf = int((geo.cs_type == 1).sum())
+    ns = int((geo.cs_type == 2).sum())
+    assert info["fluid_cs"] == nf and info["solid_cs"] == ns
+    assert info["species_cells"] == [nf * w.nx, ns * w.nx, ns * w.nx]
+    assert info["active_sites"] == (nf + ns) * w.nx
+    faces = _solid_face_count(geo)
+    assert info["iface_cs"][0] == int(((geo.cs_type == 1) & (faces > 0)).sum())
+    assert info["max_faces"][0] == int(faces[geo.cs_type == 1].max())
+    assert info["d_wall"] == pytest.approx(geo.d_wall, rel=0, abs=0)
+    assert info["bytes"] == klb.klb_lattice_bytes(klb.desc_from_workload(w)) > 0
+
+
+def test_nanotube_counts():
+    """The 512x128x128 staircase nanotube of radius 48 and shell 6."""
+    info = klb.klb_lattice_info(klb.desc_from_workload(inputs.PIPE_D3Q19_FP32))
+    assert (info["fluid_cs"], info["solid_cs"]) == (7232, 1944)
+    assert info["active_sites"] == 4_698_112
+    assert sum(info["species_cells"]) == 5_693_440
+
+
+@pytest.mark.parametrize("change,msg", [
+    (dict(tau=(0.5, 0.6, 1.0)), "relaxation"),
+    (dict(tau=(0.8, float("nan"), 1.0)), "non-finite"),
+    (dict(rho0=0.0), "rho0"),
+    (dict(nz=2), "D2Q9"),
+    (dict(shell=0), "slab"),
+    (dict(width=40), "slab"),
+])
+def test_invalid_descriptions_are_rejected(change, msg):
+    w = inputs.SLAB_D2Q9_FP64.with_(**change)
+    d = klb.desc_from_workload(w)
+    assert klb.klb_lattice_bytes(d) == 0
+    with pytest.raises(klb.KLBError) as e:
+        klb.klb_lattice_info(d)
+    assert e.value.status == 1 and msg in str(e.value)
+
+
+def test_mask_geometry_and_empty_species():
+    mask = np.array([[2, 1, 1, 2]], np.uint8)
+    d = klb.make_desc(kind=9, nx=4, ny=4, nz=1, geom=klb.KLB_GEOM_MASK, mask=mask,
+                      periodic_y=True)
+    info = klb.klb_lattice_info(d)
+    assert info["fluid_cs"] == 2 and info["solid_cs"] == 2 and math.isnan(info["d_wall"])
+    d = klb.make_desc(kind=9, nx=4, ny=4, nz=1, geom=klb.KLB_GEOM_MASK,
+                      mask=np.ones((1, 4), np.uint8), periodic_y=True)
+    with pytest.raises(klb.KLBError, match="no solid"):
+        klb.klb_lattice_info(d)

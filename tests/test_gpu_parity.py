@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances.  FP64 lattices differ from the oracle only by operation order
+and fused multiply-adds: 1e-11 relative.  FP32 lattices store deviations
+g = f - w rho0 and compute in FP32; after 10^4 steps the velocity field must
+match the FP64 oracle within 1e-5 relative L2 and the slip length within
+0.1%.  Single-step checks from a shared state use 2e-5 relative (a few FP32
+roundings of order-one relative quantities).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from klb_testutil import make_oracle, oracle_geometry, rel_l2, species_masks
+from oracle import observables_from_fields
+from paper_2403_15768_gb300 import inputs, klb
+
+pytestmark = pytest.mark.gpu
+
+SLAB = inputs.SLAB_D2Q9_FP64
+SMALL_PIPE = inputs.PIPE_D3Q19_FP32.with_(name="pipe_r8", nx=20, ny=24, nz=24, radius=8, shell=3,
+                                          couplings=(0.05, 0.02, 0.1, 0.0, 0.01))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    klb.load_library()
+
+
+def _pair(w, seed=None, eps=1e-3):
+    o = make_oracle(w)
+    lat = klb.lattice_from_workload(w)
+    if seed is not None:
+        drho, u = inputs.perturbation(w, seed, eps)
+        o.init_equilibrium(drho, u)
+        lat.init_equilibrium(drho, u)
+    else:
+        o.init_equilibrium()
+    return o, lat
+
+
+def _compare_fields(o, lat, rtol, w):
+    f = o.observe()
+    drho, u = lat.get_field()
+    masks = species_masks(o.geo, w.nx)
+    for s in range(3):
+        m = masks[s]
+        ref = f["u"][s][:, m]
+        got = u[s][:, m]
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= rtol * scale, (s, np.abs(got - ref).max(), scale)
+        assert np.abs(drho[s][m] - f["drho"][s][m]).max() <= rtol * max(
+            np.abs(f["drho"][s][m]).max(), 1e-3)
+    return f
+
+
+def test_init_state_matches_oracle():
+    for w in (SLAB, SMALL_PIPE.with_(storage="fp64")):
+        o, lat = _pair(w, seed=0)
+        g_o, U_o, _ = o.get_state()
+        g_g, U_g, U2_g = lat.get_state()
+        assert np.abs(g_g - g_o).max() < 1e-17 + 1e-14 * np.abs(g_o).max()
+        # lagged velocities are kept at interface cells only
+        iface = np.abs(U_g).sum(axis=(0, 1)) > 0
+        assert iface.any()
+        assert np.abs(U_g[:, :, iface] - U_o[:, :, iface]).max() < 1e-16
+        assert np.array_equal(U_g, U2_g)
+
+
+@pytest.mark.parametrize("seed", [None, 0])
+def test_d2q9_fp64_slab_10k_steps(seed):
+    """The D2Q9 FP64 slab channel, 10^4 steps, quiescent and perturbed starts."""
+    w = SLAB
+    o, lat = _pair(w, seed)
+    o.step(w.steps)
+    lat.step(w.steps)
+    f = _compare_fields(o, lat, 1e-11, w)
+    ob_o = observables_from_fields(o.geo, w.nx, w.rho0, f)
+    ob_g = lat.observables()
+    for k in ("flow_rate", "u_slip", "slip_length", "u_wallrow_mean"):
+        assert ob_g[k] == pytest.approx(ob_o[k], rel=1e-10), k
+    for s in range(3):
+        assert ob_g["mean_u"][s] == pytest.approx(ob_o["mean_u"][s], rel=1e-10)
+        assert ob_g["momentum"][s] == pytest.approx(ob_o["momentum"][s], rel=1e-10)
+        assert abs(ob_g["mass"][s] - ob_o["mass"][s]) < 1e-12
+    assert ob_g["residual"] == pytest.approx(ob_o["residual"], rel=1e-6, abs=1e-18)
+    assert ob_g["step"] == w.steps and ob_g["nonfinite"] == 0
+
+
+def test_d3q19_fp32_pipe_10k_steps_against_fp64_oracle():
+    """FP32 D3Q19 pipe after 10^4 steps: rel-L2 of u <= 1e-5, L_s within 0.1%."""
+    w = SMALL_PIPE
+    o, lat = _pair(w, seed=1)
+    o.step(10_000)
+    lat.step(10_000)
+    f = o.observe()
+    drho, u = lat.get_field()
+    masks = species_masks(o.geo, w.nx)
+    for s in range(3):
+        m = masks[s]
+        assert rel_l2(u[s][:, m], f["u"][s][:, m]) <= 1e-5, s
+    ob_o = observables_from_fields(o.geo, w.nx, w.rho0, f)
+    ob_g = lat.observables()
+    assert ob_g["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
+    assert ob_g["flow_rate"] == pytest.approx(ob_o["flow_rate"], rel=1e-5)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["ragged_tiles", "thin_shell", "bounceback", "slab3d", "nx1"])
+def test_short_runs_many_geometries(case, storage):
+    """Several x tiles with a ragged tail, thin shells, the bounce-back
+    interface option, a 3D slab and a single x plane; perturbed start."""
+    base = SMALL_PIPE.with_(storage=storage)
+    w = {
+        "ragged_tiles": base.with_(nx=160 + 37, ny=17, nz=15, radius=5, shell=2),
+        "thin_shell": base.with_(nx=45, ny=12, nz=12, radius=3, shell=1),
+        "bounceback": base.with_(nx=33, iface_bc="bounceback"),
+        "slab3d": base.with_(geom="slab", nx=70, ny=14, nz=3, width=6, shell=3),
+        "nx1": base.with_(nx=1),
+    }[case]
+    o, lat = _pair(w, seed=2, eps=1e-3)
+    for n in (1, 2, 50):
+        o.step(n)
+        lat.step(n)
+    _compare_fields(o, lat, 1e-11 if storage == "fp64" else 2e-4, w)
+    ob_o = o.observables()
+    ob_g = lat.observables()
+    tol = 1e-10 if storage == "fp64" else 1e-4
+    assert ob_g["flow_rate"] == pytest.approx(ob_o["flow_rate"], rel=tol)
+    assert ob_g["residual"] == pytest.approx(ob_o["residual"], rel=1e-6 if storage == "fp64" else 2e-2)
+
+
+def test_one_step_from_oracle_state():
+    """Load the oracle's state (populations and lagged velocities) into the
+    FP32 lattice, take one step on both, compare element by element."""
+    w = SMALL_PIPE.with_(nx=70)
+    o, lat = _pair(w, seed=3, eps=1e-3)
+    o.step(30)
+    g, U1, U2 = o.get_state()
+    lat.set_state(g, U1, U2, step=30)
+    g_back, _, _ = lat.get_state()
+    assert np.abs(g_back - g).max() <= 1e-7 * np.abs(g).max()
+    o.step(1)
+    lat.step(1)
+    g_o, _, _ = o.get_state()
+    g_g, _, _ = lat.get_state()
+    assert np.abs(g_g - g_o).max() <= 2e-5 * np.abs(g_o).max()
+    assert lat.nstep == 31
+
+
+def test_lagged_pair_mask_geometry():
+    """Fluid row between solid rows (periodic y): the averaged-lag pair
+    recurrence, on the GPU in FP64."""
+    mask = np.array([[2, 1]], np.uint8)
+    w = inputs.Workload(name="pair", kind=19, geom="mask", nx=3, ny=2, nz=1, tau=(0.8, 0.6, 1.0),
+                        G=(0.0, 0.0, 0.0), couplings=(0.07, 0.0, 0.0, 0.0, 0.0), storage="fp64",
+                        extra={"mask": mask, "periodic_y": True, "periodic_z": True})
+    lat = klb.lattice_from_workload(w)
+    u = np.zeros((3, 3, 1, 2, 3))
+    u[0, 0] = 0.02
+    u[1, 0] = 0.005
+    lat.init_equilibrium(None, u)
+    k = 2 * 0.07 * 2.0
+    D = {-2: 0.015, -1: 0.015, 0: (1 - k / 2) * 0.015}
+    for n in range(30):
+        if n >= 1:
+            D[n] = D[n - 1] - (k / 2) * (0.5 * (D[n - 2] + D[n - 3]) + 0.5 * (D[n - 1] + D[n - 2]))
+        _, uf = lat.get_field()
+        assert abs(uf[0, 0, 0, 1].mean() - uf[1, 0, 0, 0].mean() - D[n]) < 1e-15
+        lat.step(1)
+
+
+def test_free_acceleration_full_nanotube():
+    """Full 512x128x128 nanotube in the benchmark's launch configuration,
+    no friction: every fluid cell has u_x = G (n + 1/2) (FP32, relative 1e-5),
+    and the species masses stay zero."""
+    w = inputs.PIPE_D3Q19_FP32.with_(couplings=(0.0,) * 5, G=(1e-5, 0.0, 0.0))
+    lat = klb.lattice_from_workload(w)
+    lat.step(200)
+    ob = lat.observables()
+    n_fluid = lat.species_cells(0)
+    assert ob["flow_rate"] == pytest.approx(1e-5 * 200.5 * n_fluid / w.nx, rel=1e-5)
+    assert ob["mean_u"][0] == pytest.approx(1e-5 * 200.5, rel=1e-5)
+    assert abs(ob["mean_u"][1]) < 1e-12 and abs(ob["mean_u"][2]) < 1e-12
+    assert ob["nonfinite"] == 0
+    assert ob["residual"] == pytest.approx(1e-5, rel=1e-3)
+
+
+def test_full_nanotube_invariants_and_symmetry():
+    """Full 512x128x128 nanotube with its seeded couplings: masses conserved,
+    x-momentum balance of one step, eight-fold symmetry of the flow."""
+    w = inputs.PIPE_D3Q19_FP32
+    lat = klb.lattice_from_workload(w)
+    lat.step(400)
+    ob0 = lat.observables()
+    drho, u = lat.get_field()
+    geo = oracle_geometry(w)
+    for s in range(3):
+        ux = u[s, 0, :, :, 0]  # (z, y) at x = 0
+        scale = np.abs(ux).max()
+        assert scale > 0
+        for img in (ux.T, ux[::-1, :], ux[:, ::-1]):
+            assert np.abs(ux - img).max() <= 1e-5 * scale
+        # x-invariance of a quiescent start
+        assert np.abs(u[s, 0] - u[s, 0, :, :, :1]).max() <= 1e-6 * scale
+    for s in range(3):
+        assert abs(ob0["mass"][s]) < 1e-6 * lat.species_cells(s) * 1e-3
+    assert ob0["nonfinite"] == 0 and not math.isnan(ob0["slip_length"])
+
+
+def test_one_step_full_nanotube_from_gpu_state():
+    """Full 512x128x128 nanotube in the benchmark's launch configuration: the
+    FP64 oracle takes one step from the GPU's FP32 state after 300 steps of a
+    perturbed start, and the GPU's next step must match it (relative L2 of
+    every species' velocity field within 1e-5)."""
+    avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    if avail < 48e9:
+        pytest.skip("needs ~40 GB of host memory for the FP64 oracle of the full box")
+    w = inputs.PIPE_D3Q19_FP32
+    lat = klb.lattice_from_workload(w)
+    drho0, u0 = inputs.perturbation(w, 4, 1e-4)
+    lat.init_equilibrium(drho0, u0)
+    del drho0, u0
+    lat.step(300)
+    g, U1, U2 = lat.get_state()
+    o = make_oracle(w)
+    o.set_state(g, U1, U2, step=300)
+    del g, U1, U2
+    o.step(1)
+    lat.step(1)
+    uo = o.observe()["u"]
+    _, ug = lat.get_field()
+    masks = species_masks(o.geo, w.nx)
+    for s in range(3):
+        m = masks[s]
+        assert rel_l2(ug[s][:, m], uo[s][:, m]) <= 1e-5
+
+
+def test_unstable_state_is_reported():
+    """A non-finite value staged from the host is caught by the observation
+    pass and reported as KLB_EUNSTABLE."""
+    w = SMALL_PIPE
+    lat = klb.lattice_from_workload(w)
+    drho, u = inputs.perturbation(w, 0, 1e-3)
+    geo = oracle_geometry(w)
+    z, y = np.argwhere(geo.cs_type == 1)[0]
+    u[0, 0, z, y, 3] = np.nan
+    lat.init_equilibrium(drho, u)
+    lat.step(2)
+    with pytest.raises(klb.KLBError) as e:
+        lat.observables()
+    assert e.value.status == 4
+    ob = lat.observables(allow_unstable=True)
+    assert ob["nonfinite"] > 0
+
+
+def test_coupling_validation_and_buffer_size():
+    import torch
+
+    w = SMALL_PIPE
+    lat = klb.lattice_from_workload(w)
+    with pytest.raises(klb.KLBError, match="stability"):
+        lat.set_couplings(0.3, 0.3, 0.1)
+    with pytest.raises(klb.KLBError, match="non-finite"):
+        lat.set_couplings(float("inf"), 0.0, 0.0)
+    lat.set_couplings(-0.01, 0.02, 0.05, 0.0, 0.01)  # negative friction within the bound
+    lat.step(10)
+    assert lat.observables()["nonfinite"] == 0
+    d = klb.desc_from_workload(w)
+    n = klb.klb_lattice_bytes(d)
+    buf = torch.empty(n - 256, dtype=torch.uint8, device="cuda")
+    import ctypes
+    h = ctypes.c_void_p()
+    st = klb.load_library().klb_create_lattice(ctypes.byref(d), ctypes.c_void_p(buf.data_ptr()),
+                                               n - 256, None, ctypes.byref(h))
+    assert st == 2 and not h.value
