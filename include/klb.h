@@ -201,6 +201,38 @@ klb_status klb_step(klb_lattice *lat, int64_t nsteps);
  * non-finite value was seen. */
 klb_status klb_observables(klb_lattice *lat, klb_obs *out);
 
+/*
+ * Allocation-free variant of klb_observables().  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory.  Typical ones embed the library in a host application that owns
+ * the device allocator (a fixed pool, or a process running under a hard
+ * device-memory cap) and hands out the lattice buffer once; they cannot ask
+ * for more, and may want the lattice buffer to hold nothing but the solver
+ * state while observations run.
+ *
+ * Same inputs and output as klb_observables() (the lattice state is read, the
+ * observables are written to *out on the host).  The per-block FP64 partial
+ * sums and the final sums live in a static device array of this library
+ * instead of the lattice buffer: KLB_STATIC_MAX_BLOCKS blocks of 18 doubles
+ * plus 32 doubles (about 7.1 MB), held on every GPU that loads the library
+ * until the process exits.  Nothing is allocated: no cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ *
+ * - Lattices whose observation pass needs more than KLB_STATIC_MAX_BLOCKS
+ *   thread blocks (one per 128 x positions of each cross-section cell) are
+ *   rejected with KLB_EINVAL and a message naming the limit.
+ * - The first call on a device looks up the device address of the array
+ *   (once per device, with that device current); make that first call before
+ *   any stream capture.
+ * - Every call shares the one array and it keeps the last call's contents.
+ *   Each call overwrites every entry it reads, so nothing needs clearing, but
+ *   calls that overlap on the GPU (other streams, other host threads, other
+ *   lattices) race on it: serialise them.
+ * Synchronises the lattice's stream.
+ */
+#define KLB_STATIC_MAX_BLOCKS 49152
+klb_status klb_observables_static(klb_lattice *lat, klb_obs *out);
+
 /* Density deviations drho[3][ncell] and velocities u[3][3][ncell] of the
  * current step, host, box layout (either may be NULL).  Synchronises. */
 klb_status klb_get_field(klb_lattice *lat, double *drho, double *u);

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libklb.so")
-SOURCES = ["klb_kernels.cu", "klb_geometry.cpp", "klb_api.cpp"]
+SOURCES = ["klb_kernels.cu", "klb_geometry.cpp", "klb_api.cpp", "klb_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -184,6 +184,45 @@ klb_status init_from_fields(klb_lattice *L, const double *drho, const double *u)
     return sync(L);
 }
 
+// Observables from the final sums, for klb_observables_static (the same
+// definitions as klb_observables).
+klb_status finish_observables(klb_lattice *L, const double *S, klb_obs *out)
+{
+    const Geometry &g = L->geo;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    std::memset(out, 0, sizeof *out);
+    out->step = L->step;
+    out->flow_rate = S[kSumUxFluid] / g.nx;
+    out->d_wall = g.has_fit ? g.d_wall : nan;
+    const double n = S[kSumFitN], s2 = S[kSumFitD2], s4 = S[kSumFitD4];
+    const double su = S[kSumFitU], su2 = S[kSumFitUD2];
+    const double det = n * s4 - s2 * s2;
+    if (g.has_fit && n >= 2 && det != 0.0) {
+        out->fit_B = (n * su2 - s2 * su) / det;
+        out->fit_A = (su - out->fit_B * s2) / n;
+        out->u_slip = out->fit_A + out->fit_B * g.d_wall * g.d_wall;
+        out->dudn_wall = std::fabs(2.0 * out->fit_B * g.d_wall);
+        out->slip_length = out->dudn_wall != 0.0 ? out->u_slip / out->dudn_wall
+                                                 : std::numeric_limits<double>::infinity();
+    } else {
+        out->fit_A = out->fit_B = out->u_slip = out->dudn_wall = out->slip_length = nan;
+    }
+    out->u_wallrow_mean = S[kSumWallN] > 0 ? S[kSumWallU] / S[kSumWallN] : nan;
+    const double ncells[3] = {(double)g.rows[kFluid].size() * g.nx,
+                              (double)g.rows[kSolid].size() * g.nx,
+                              (double)g.rows[kSolid].size() * g.nx};
+    const double usum[3] = {S[kSumUxFluid], S[kSumUxE], S[kSumUxP]};
+    for (int s = 0; s < 3; ++s) {
+        out->mean_u[s] = usum[s] / ncells[s];
+        out->momentum[s] = S[kSumMomW + s];
+        out->mass[s] = S[kSumMassW + s];
+    }
+    out->residual = L->since_reset >= 2 ? S[kSumResidual] : nan;
+    out->nonfinite = (int64_t)S[kSumNonfinite];
+    if (out->nonfinite > 0) return fail(L, KLB_EUNSTABLE, "non-finite density or velocity");
+    return KLB_OK;
+}
+
 bool finite5(const klb_couplings &c)
 {
     return std::isfinite(c.g_we) && std::isfinite(c.g_wp) && std::isfinite(c.g_ep) &&
@@ -366,6 +405,33 @@ klb_status klb_observables(klb_lattice *L, klb_obs *out)
     out->nonfinite = (int64_t)S[kSumNonfinite];
     if (out->nonfinite > 0) return fail(L, KLB_EUNSTABLE, "non-finite density or velocity");
     return KLB_OK;
+}
+
+klb_status klb_observables_static(klb_lattice *L, klb_obs *out)
+{
+    if (!L || !out) return fail(L, KLB_EINVAL, "null argument");
+    double *partials = nullptr, *sums = nullptr;
+    size_t max_blocks = 0;
+    KLB_CUDA(L, static_scratch(&partials, &sums, &max_blocks));
+    if ((size_t)nblocks(L) > max_blocks)
+        return fail(L, KLB_EINVAL,
+                    "observation pass needs " + std::to_string(nblocks(L)) +
+                        " blocks, more than the static scratch holds (KLB_STATIC_MAX_BLOCKS = " +
+                        std::to_string(max_blocks) + ")");
+    KLB_CUDA(L, with_args(L, [&](void *a) {
+                 if (L->desc.storage == KLB_FP64)
+                     static_cast<StepArgs<double> *>(a)->partials = partials;
+                 else
+                     static_cast<StepArgs<float> *>(a)->partials = partials;
+                 return launch_step(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L),
+                                    L->plan.bx, L->stream);
+             }));
+    KLB_CUDA(L, launch_finalize(partials, nblocks(L), sums, L->stream));
+    double S[kNumSums];
+    KLB_CUDA(L, cudaMemcpyAsync(S, sums, sizeof S, cudaMemcpyDeviceToHost, L->stream));
+    klb_status st = sync(L);
+    if (st != KLB_OK) return st;
+    return finish_observables(L, S, out);
 }
 
 klb_status klb_get_field(klb_lattice *L, double *drho, double *u)

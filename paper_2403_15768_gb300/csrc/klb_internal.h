@@ -118,4 +118,8 @@ cudaError_t launch_init(int Q, int storage, const void *args, int nblocks, int b
                         cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s);
 
+// Static scratch of klb_observables_static (klb_static.cu): device addresses
+// of its partial-sum rows and final sums on the current device.
+cudaError_t static_scratch(double **partials, double **sums, size_t *max_blocks);
+
 }  // namespace klb

@@ -19,13 +19,15 @@ import numpy as np
 from . import build as _build
 
 KLB_D2Q9, KLB_D3Q19 = 9, 19
+KLB_STATIC_MAX_BLOCKS = 49152
 KLB_GEOM_SLAB, KLB_GEOM_PIPE, KLB_GEOM_MASK = 0, 1, 2
 KLB_FP64, KLB_FP32 = 0, 1
 KLB_IFACE_SPECULAR, KLB_IFACE_BOUNCEBACK = 0, 1
 STATUS = {0: "KLB_OK", 1: "KLB_EINVAL", 2: "KLB_ENOMEM", 3: "KLB_ECUDA", 4: "KLB_EUNSTABLE",
           5: "KLB_ETIMEOUT", 6: "KLB_ESTATE"}
 EXPORTS = ["klb_lattice_bytes", "klb_lattice_info", "klb_create_lattice", "klb_set_couplings",
-           "klb_init_equilibrium", "klb_step", "klb_observables", "klb_get_field",
+           "klb_init_equilibrium", "klb_step", "klb_observables", "klb_observables_static",
+           "klb_get_field",
            "klb_get_state", "klb_set_state", "klb_get_step", "klb_species_cells",
            "klb_destroy", "klb_last_error"]
 
@@ -103,6 +105,8 @@ def load_library(path: str | None = None):
     lib.klb_step.argtypes = [P, I64]
     lib.klb_observables.restype = I32
     lib.klb_observables.argtypes = [P, ctypes.POINTER(klb_obs)]
+    lib.klb_observables_static.restype = I32
+    lib.klb_observables_static.argtypes = [P, ctypes.POINTER(klb_obs)]
     lib.klb_get_field.restype = I32
     lib.klb_get_field.argtypes = [P, P, P]
     lib.klb_get_state.restype = I32
