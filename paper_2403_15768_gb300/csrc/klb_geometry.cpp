@@ -246,6 +246,7 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
                 ri.src[i] = (int32_t)(((long)sdir * nr + srow) * g.nxp);
                 if (sx == 1) ri.xm |= 1u << i;   // source at x - 1
                 if (sx == -1) ri.xp |= 1u << i;  // source at x + 1
+                if (cx != 0 && sx == 0) ri.flags |= kXBounce;
             }
         }
         // Every population must be pulled exactly once (mass conservation).

@@ -29,12 +29,13 @@ struct RowInfo {
     int32_t nface;              // number of fluid/solid faces
     int32_t partner[kMaxFaces]; // interface slots of the rows across those faces
     float d2;                   // fluid rows: squared distance to centre plane / axis
-    int32_t flags;              // fluid rows: bit 0 in the slip fit, bit 1 wall row
+    int32_t flags;              // bit 0 in the slip fit, bit 1 wall row (fluid rows);
+                                // bit 2: some direction with c_x != 0 bounces back
     int32_t pad[3];
 };
 static_assert(sizeof(RowInfo) == 128, "RowInfo is one 128-byte line");
 
-enum RowFlags { kFitRow = 1, kWallRow = 2 };
+enum RowFlags { kFitRow = 1, kWallRow = 2, kXBounce = 4 };
 
 // Indices of the FP64 partial sums reduced by the observation kernel.
 enum SumIndex {
@@ -101,6 +102,7 @@ struct StepArgs {
     const T *U1[2], *U2[2], *U3[2];  // lagged velocities u(n-1), u(n-2), u(n-3)
     T *U0[2];                        // u(n) written here (step mode)
     int nx, nxp, nchunk, nbw;
+    int snchunk, snbw, snitems;      // staged step: 128-wide x chunks, water items, all items
     int n_rows[2], n_slots[2];
     T rho0, om[3], G[3];
     T g_we, g_wp, g_ep, g_ec, g_pc;

@@ -1,7 +1,7 @@
 // CUDA kernels of the KLB step for sm_103a.
 //
-// One fused kernel per lattice step updates all three species (Sec. 4: one
-// population set per species, {h_i, e_i, p_i}):
+// One fused kernel per lattice step (k_step) updates all three species
+// (Sec. 4: one population set per species, {h_i, e_i, p_i}):
 //   pull-stream (boundary rules of Sec. 4.2, precomputed per row) ->
 //   moments -> interface friction (Eq. 27) from lagged velocities ->
 //   trapezoidal electron-phonon friction and crystal sinks (Eqs. 12, 13, 16) ->
@@ -9,15 +9,16 @@
 //   store (A-B: the state is read from one buffer and written to the other).
 //
 // Layout: structure of arrays, per species [direction][row][x] with rows of
-// nxp elements (x fastest, rows padded to 32 elements), so every load and
-// store of a warp is a contiguous run of x.  A block covers up to 128
-// consecutive x of one row: the row table (sources, x shifts, interface
-// partners) is block-uniform.  Water blocks come first in the grid, then the
-// solid blocks, each of which updates the electrons and phonons of its row.
+// nxp elements (x fastest, rows padded to 32 elements), so every copy and
+// store of a warp is a contiguous run of x.  A work item is 128 consecutive
+// x of one row; the row table (sources, x shifts, interface partners) is
+// item-uniform.  Water items come first, then the solid items, each of which
+// updates the electrons and phonons of its row.
 //
-// The same per-cell code serves three modes: the step, the observation pass
-// (velocities of the current and previous step reduced in FP64, no stores of
-// populations) and the field pass (velocities written to a scratch field).
+// k_step is persistent and stages its sources in shared memory with
+// asynchronous copies.  k_lattice runs the same per-cell arithmetic, loading
+// straight from global memory, for the observation pass (velocities of the
+// current and previous step reduced in FP64) and the field pass.
 
 #include <cuda_runtime.h>
 
@@ -85,21 +86,54 @@ __device__ __forceinline__ void pull(const T *__restrict__ in, const RowInfo &R,
     }
 }
 
+// c_i . v with only the non-zero velocity components (no additions of 0,
+// which IEEE signed zeros keep the compiler from dropping).
+template <int Q, typename T>
+__device__ __forceinline__ T cdot(int i, const T v[3])
+{
+    const int c[3] = {cx<Q>(i), cy<Q>(i), cz<Q>(i)};
+    T r = T(0);
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] == 0) continue;
+        if (!any)
+            r = c[a] > 0 ? v[a] : -v[a];
+        else
+            r = c[a] > 0 ? r + v[a] : r - v[a];
+        any = true;
+    }
+    return r;
+}
+
+// Sum of +-g_i over the directions with c_ia = +-1 (first term not added to 0).
+template <int Q, typename T>
+__device__ __forceinline__ T cmoment(int a, const T g[Q])
+{
+    T r = T(0);
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int c = a == 0 ? cx<Q>(i) : (a == 1 ? cy<Q>(i) : cz<Q>(i));
+        if (c == 0) continue;
+        if (!any)
+            r = c > 0 ? g[i] : -g[i];
+        else
+            r = c > 0 ? r + g[i] : r - g[i];
+        any = true;
+    }
+    return r;
+}
+
 template <int Q, typename T>
 __device__ __forceinline__ void moments(const T g[Q], T &drho, T j[3])
 {
-    drho = T(0);
-    j[0] = j[1] = j[2] = T(0);
+    drho = g[0];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += g[i];
-        if (cx<Q>(i) > 0) j[0] += g[i];
-        if (cx<Q>(i) < 0) j[0] -= g[i];
-        if (cy<Q>(i) > 0) j[1] += g[i];
-        if (cy<Q>(i) < 0) j[1] -= g[i];
-        if (cz<Q>(i) > 0) j[2] += g[i];
-        if (cz<Q>(i) < 0) j[2] -= g[i];
-    }
+    for (int i = 1; i < Q; ++i) drho += g[i];
+    j[0] = cmoment<Q, T>(0, g);
+    j[1] = cmoment<Q, T>(1, g);
+    j[2] = Q == 19 ? cmoment<Q, T>(2, g) : T(0);
 }
 
 // Index of the direction with velocity (a, b, c), at compile time.
@@ -138,23 +172,22 @@ __device__ __forceinline__ void collide_store(T g[Q], const Cell<T> &c, const T 
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T w = T(wt<Q>(i));
-        T cu = T(0), cF = T(0);
-        if (cx<Q>(i)) { cu += T(cx<Q>(i)) * c.u[0]; cF += T(cx<Q>(i)) * c.F[0]; }
-        if (cy<Q>(i)) { cu += T(cy<Q>(i)) * c.u[1]; cF += T(cy<Q>(i)) * c.F[1]; }
-        if (cz<Q>(i)) { cu += T(cz<Q>(i)) * c.u[2]; cF += T(cz<Q>(i)) * c.F[2]; }
+        if (i == 0) {  // rest population: c = 0
+            g[0] = om1 * g[0] + (om * w) * e0 + (fo * w) * m3uF;
+            continue;
+        }
+        const T cu = cdot<Q, T>(i, c.u);
+        const T cF = cdot<Q, T>(i, c.F);
         const T teq = e0 + cu * (r3 + r45 * cu);
         const T tF = m3uF + cF * (T(3) + T(9) * cu);
         g[i] = om1 * g[i] + (om * w) * teq + (fo * w) * tF;
     }
     if (sizeof(T) == 4) {
-        T m = T(0), p[3] = {T(0), T(0), T(0)};
+        T m = g[0];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            m += g[i];
-            if (cx<Q>(i)) p[0] += T(cx<Q>(i)) * g[i];
-            if (cy<Q>(i)) p[1] += T(cy<Q>(i)) * g[i];
-            if (cz<Q>(i)) p[2] += T(cz<Q>(i)) * g[i];
-        }
+        for (int i = 1; i < Q; ++i) m += g[i];
+        const T p[3] = {cmoment<Q, T>(0, g), cmoment<Q, T>(1, g),
+                        Q == 19 ? cmoment<Q, T>(2, g) : T(0)};
         g[0] += c.drho - m;
         const T hx = T(0.5) * ((j[0] + c.F[0]) - p[0]);
         const T hy = T(0.5) * ((j[1] + c.F[1]) - p[1]);
@@ -178,25 +211,26 @@ __device__ __forceinline__ T lagged(const T *U1, const T *U2, int idx)
     return T(0.5) * (U1[idx] + U2[idx]);
 }
 
-// Water cell: moments, interface friction, Guo velocity.  U1/U2 are the
-// velocities of the two previous steps of the same time level as `in`.
+// Water cell given its streamed populations g: moments, interface friction,
+// Guo velocity.  U1/U2 are the velocities of the two steps before the time
+// level of g; R is the row's table (global or shared memory).
 template <int Q, typename T>
-__device__ __forceinline__ void water_cell(const StepArgs<T> &p, const T *__restrict__ in,
-                                           const T *Uw1, const T *Uw2, const T *Us1,
-                                           const T *Us2, const RowInfo &R, int x, int xm1,
-                                           int xp1, T g[Q], Cell<T> &c, T j[3])
+__device__ __forceinline__ void water_math(const StepArgs<T> &p, const T *Uw1, const T *Uw2,
+                                           const T *Us1, const T *Us2, const RowInfo &R, int x,
+                                           const T g[Q], Cell<T> &c, T j[3])
 {
-    pull<Q, T>(in, R, x, xm1, xp1, g);
     moments<Q, T>(g, c.drho, j);
     c.F[0] = p.G[0];
     c.F[1] = p.G[1];
     c.F[2] = p.G[2];
-    if (R.slot >= 0) {
+    const int slot = R.slot;
+    if (slot >= 0) {
         const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
+        const int nface = R.nface;
         for (int a = 0; a < 3; ++a) {
-            const T uw = lagged(Uw1, Uw2, (a * ns_w + R.slot) * nxp + x);
+            const T uw = lagged(Uw1, Uw2, (a * ns_w + slot) * nxp + x);
             T f = T(0);
-            for (int k = 0; k < R.nface; ++k) {
+            for (int k = 0; k < nface; ++k) {
                 const int q = R.partner[k];
                 const T de = uw - lagged(Us1, Us2, (a * ns_s + q) * nxp + x);
                 const T dp = uw - lagged(Us1, Us2, ((a + 3) * ns_s + q) * nxp + x);
@@ -210,26 +244,35 @@ __device__ __forceinline__ void water_cell(const StepArgs<T> &p, const T *__rest
     for (int a = 0; a < 3; ++a) c.u[a] = (j[a] + T(0.5) * c.F[a]) * rinv;
 }
 
-// Solid cell: electrons and phonons of one cell.
 template <int Q, typename T>
-__device__ __forceinline__ void solid_cell(const StepArgs<T> &p, const T *__restrict__ in_e,
-                                           const T *__restrict__ in_p, const T *Uw1,
-                                           const T *Uw2, const T *Us1, const T *Us2,
-                                           const RowInfo &R, int x, int xm1, int xp1, T ge[Q],
-                                           T gp[Q], Cell<T> &ce, Cell<T> &cp, T je[3], T jp[3])
+__device__ __forceinline__ void water_cell(const StepArgs<T> &p, const T *__restrict__ in,
+                                           const T *Uw1, const T *Uw2, const T *Us1,
+                                           const T *Us2, const RowInfo &R, int x, int xm1,
+                                           int xp1, T g[Q], Cell<T> &c, T j[3])
 {
-    pull<Q, T>(in_e, R, x, xm1, xp1, ge);
-    pull<Q, T>(in_p, R, x, xm1, xp1, gp);
+    pull<Q, T>(in, R, x, xm1, xp1, g);
+    water_math<Q, T>(p, Uw1, Uw2, Us1, Us2, R, x, g, c, j);
+}
+
+// Electrons and phonons of one solid cell given their streamed populations.
+template <int Q, typename T>
+__device__ __forceinline__ void solid_math(const StepArgs<T> &p, const T *Uw1, const T *Uw2,
+                                           const T *Us1, const T *Us2, const RowInfo &R, int x,
+                                           const T ge[Q], const T gp[Q], Cell<T> &ce,
+                                           Cell<T> &cp, T je[3], T jp[3])
+{
     moments<Q, T>(ge, ce.drho, je);
     moments<Q, T>(gp, cp.drho, jp);
     T Fe[3] = {T(0), T(0), T(0)}, Fp[3] = {T(0), T(0), T(0)};
-    if (R.slot >= 0) {
+    const int slot = R.slot;
+    if (slot >= 0) {
         const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
+        const int nface = R.nface;
         for (int a = 0; a < 3; ++a) {
-            const T ue = lagged(Us1, Us2, (a * ns_s + R.slot) * nxp + x);
-            const T up = lagged(Us1, Us2, ((a + 3) * ns_s + R.slot) * nxp + x);
+            const T ue = lagged(Us1, Us2, (a * ns_s + slot) * nxp + x);
+            const T up = lagged(Us1, Us2, ((a + 3) * ns_s + slot) * nxp + x);
             T fe = T(0), fp = T(0);
-            for (int k = 0; k < R.nface; ++k) {
+            for (int k = 0; k < nface; ++k) {
                 const T uw = lagged(Uw1, Uw2, (a * ns_w + R.partner[k]) * nxp + x);
                 fe += p.g_we * (uw - ue);
                 fp += p.g_wp * (uw - up);
@@ -255,6 +298,18 @@ __device__ __forceinline__ void solid_cell(const StepArgs<T> &p, const T *__rest
         ce.F[a] = Fe[a] - p.g_ep * (ue - up) - p.g_ec * ue;
         cp.F[a] = Fp[a] + p.g_ep * (ue - up) - p.g_pc * up;
     }
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void solid_cell(const StepArgs<T> &p, const T *__restrict__ in_e,
+                                           const T *__restrict__ in_p, const T *Uw1,
+                                           const T *Uw2, const T *Us1, const T *Us2,
+                                           const RowInfo &R, int x, int xm1, int xp1, T ge[Q],
+                                           T gp[Q], Cell<T> &ce, Cell<T> &cp, T je[3], T jp[3])
+{
+    pull<Q, T>(in_e, R, x, xm1, xp1, ge);
+    pull<Q, T>(in_p, R, x, xm1, xp1, gp);
+    solid_math<Q, T>(p, Uw1, Uw2, Us1, Us2, R, x, ge, gp, ce, cp, je, jp);
 }
 
 // ---------------------------------------------------------------------------
@@ -323,18 +378,11 @@ __global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
         const int nxp = p.nxp;
         if (water) {
             const RowInfo &R = p.rows[kFluid][row];
-            const int stride = p.n_rows[kFluid] * nxp, base = row * nxp + x;
             T g[Q], j[3];
             Cell<T> c;
             water_cell<Q, T>(p, p.in[0], p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R,
                              x, xm1, xp1, g, c, j);
-            if (MODE == kModeStep) {
-                if (R.slot >= 0) {
-                    const int ns = p.n_slots[kFluid];
-                    for (int a = 0; a < 3; ++a) p.U0[kFluid][(a * ns + R.slot) * nxp + x] = c.u[a];
-                }
-                collide_store<Q, T>(g, c, j, p.rho0, p.om[0], p.out[0], stride, base);
-            } else if (MODE == kModeField) {
+            if (MODE == kModeField) {
                 T *f = p.field;
                 f[row * nxp + x] = c.drho;
                 for (int a = 0; a < 3; ++a) f[((a + 1) * p.n_rows[kFluid] + row) * nxp + x] = c.u[a];
@@ -366,22 +414,11 @@ __global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
             }
         } else {
             const RowInfo &R = p.rows[kSolid][row];
-            const int stride = p.n_rows[kSolid] * nxp, base = row * nxp + x;
             T ge[Q], gp[Q], je[3], jp[3];
             Cell<T> ce, cp;
             solid_cell<Q, T>(p, p.in[1], p.in[2], p.U1[kFluid], p.U2[kFluid], p.U1[kSolid],
                              p.U2[kSolid], R, x, xm1, xp1, ge, gp, ce, cp, je, jp);
-            if (MODE == kModeStep) {
-                if (R.slot >= 0) {
-                    const int ns = p.n_slots[kSolid];
-                    for (int a = 0; a < 3; ++a) {
-                        p.U0[kSolid][(a * ns + R.slot) * nxp + x] = ce.u[a];
-                        p.U0[kSolid][((a + 3) * ns + R.slot) * nxp + x] = cp.u[a];
-                    }
-                }
-                collide_store<Q, T>(ge, ce, je, p.rho0, p.om[1], p.out[1], stride, base);
-                collide_store<Q, T>(gp, cp, jp, p.rho0, p.om[2], p.out[2], stride, base);
-            } else if (MODE == kModeField) {
+            if (MODE == kModeField) {
                 const int nrw = p.n_rows[kFluid], nrs = p.n_rows[kSolid];
                 T *fe = p.field + (size_t)4 * nrw * nxp;
                 T *fp = fe + (size_t)4 * nrs * nxp;
@@ -483,15 +520,251 @@ __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ par
 }
 
 // ---------------------------------------------------------------------------
+// Staged persistent step kernel.
+//
+// Each CTA walks work items (one row, 128 consecutive x) with a stride of the
+// grid size.  The Q (water) or 2Q (electron + phonon) source-row segments of
+// an item, with one halo element on each side, are copied into shared memory
+// by asynchronous 16-byte copies (cp.async), double-buffered: the next
+// item's copies are in flight while the current item computes, so memory
+// parallelism does not depend on how many threads are resident.  The row
+// table of the item after next is fetched the same way.  Stores go straight
+// to global memory, coalesced along x.
+
+constexpr int kSegPad = 4;                  // data at element 4: 16-byte aligned
+constexpr int kSeg = kBlockX + 2 * kSegPad;  // elements per staged segment
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct Item {
+    int cls, row, x0, n;
+};
+
+template <typename T>
+__device__ __forceinline__ Item decode_item(const StepArgs<T> &p, int k)
+{
+    Item it;
+    it.cls = k < p.snbw ? kFluid : kSolid;
+    const int kk = it.cls == kFluid ? k : k - p.snbw;
+    it.row = kk / p.snchunk;
+    it.x0 = (kk - it.row * p.snchunk) * kBlockX;
+    it.n = min(kBlockX, p.nx - it.x0);
+    return it;
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_table(const StepArgs<T> &p, const Item &it, RowInfo *dst)
+{
+    if (threadIdx.x < sizeof(RowInfo) / 16) {
+        const char *src = reinterpret_cast<const char *>(p.rows[it.cls] + it.row);
+        cp_async16(reinterpret_cast<char *>(dst) + 16 * threadIdx.x, src + 16 * threadIdx.x);
+    }
+}
+
+// Source row (element pointer at x = 0) of staged segment d of an item.
+template <int Q, typename T>
+__device__ __forceinline__ const T *segment_row(const StepArgs<T> &p, const Item &it,
+                                               const RowInfo &R, int d)
+{
+    const int s = it.cls == kFluid ? 0 : (d < Q ? 1 : 2);
+    const int i = d < Q ? d : d - Q;
+    return p.in[s] + R.src[i];
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void issue_item(const StepArgs<T> &p, const Item &it, const RowInfo &R,
+                                           T *stage)
+{
+    constexpr int EPC = 16 / sizeof(T);    // elements per 16-byte copy
+    constexpr int L = kBlockX / EPC;       // copy lanes per full segment
+    constexpr int G = kBlockX / L;         // segments per pass of the block
+    const int nseg = it.cls == kFluid ? Q : 2 * Q;
+    const int nfull = it.n / EPC;
+    const int rem = it.n - nfull * EPC;
+    const int t = threadIdx.x;
+    const int c = t % L;
+    if (c < nfull) {
+        for (int d = t / L; d < nseg; d += G)
+            cp_async16(stage + d * kSeg + kSegPad + c * EPC,
+                       segment_row<Q, T>(p, it, R, d) + it.x0 + c * EPC);
+    }
+    // The two periodic halo elements of every segment.
+    const int xl = it.x0 == 0 ? p.nx - 1 : it.x0 - 1;
+    const int xr = it.x0 + it.n == p.nx ? 0 : it.x0 + it.n;
+    for (int f = t; f < 2 * nseg; f += kBlockX) {
+        const int d = f >> 1;
+        const bool right = f & 1;
+        cp_async_small<sizeof(T)>(stage + d * kSeg + (right ? kSegPad + it.n : kSegPad - 1),
+                                  segment_row<Q, T>(p, it, R, d) + (right ? xr : xl));
+    }
+    // Tail elements of a ragged chunk.
+    if (rem) {
+        for (int f = t; f < nseg * rem; f += kBlockX) {
+            const int d = f / rem, e = f - d * rem;
+            cp_async_small<sizeof(T)>(stage + d * kSeg + kSegPad + nfull * EPC + e,
+                                      segment_row<Q, T>(p, it, R, d) + it.x0 + nfull * EPC + e);
+        }
+    }
+}
+
+// Populations of segment group `base` at thread t.  Direction i pulls from
+// x - c_ix except on rows where a direction with c_ix != 0 bounces back
+// (flag kXBounce), whose shifts come from the row's bit masks.
+template <int Q, typename T>
+__device__ __forceinline__ void load_staged(const T *stage, const RowInfo &R, int base, int t,
+                                            T g[Q])
+{
+    const T *s0 = stage + base * kSeg + kSegPad + t;
+    if (!(R.flags & kXBounce)) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = s0[i * kSeg - cx<Q>(i)];
+    } else {
+        const uint32_t xm = R.xm, xp = R.xp;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int sh = (int)((xp >> i) & 1u) - (int)((xm >> i) & 1u);
+            g[i] = s0[i * kSeg + sh];
+        }
+    }
+}
+
+template <int Q, typename T>
+__device__ __forceinline__ void compute_item(const StepArgs<T> &p, const Item &it,
+                                             const RowInfo &R, const T *stage)
+{
+    const int t = threadIdx.x;
+    if (t >= it.n) return;
+    const int x = it.x0 + t, nxp = p.nxp;
+    if (it.cls == kFluid) {
+        T g[Q], j[3];
+        Cell<T> c;
+        load_staged<Q, T>(stage, R, 0, t, g);
+        water_math<Q, T>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, x, g, c, j);
+        if (R.slot >= 0) {
+            const int ns = p.n_slots[kFluid];
+            for (int a = 0; a < 3; ++a) p.U0[kFluid][(a * ns + R.slot) * nxp + x] = c.u[a];
+        }
+        collide_store<Q, T>(g, c, j, p.rho0, p.om[0], p.out[0], p.n_rows[kFluid] * nxp,
+                            it.row * nxp + x);
+    } else {
+        T ge[Q], gp[Q], je[3], jp[3];
+        Cell<T> ce, cp;
+        load_staged<Q, T>(stage, R, 0, t, ge);
+        load_staged<Q, T>(stage, R, Q, t, gp);
+        solid_math<Q, T>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, x, ge, gp,
+                         ce, cp, je, jp);
+        if (R.slot >= 0) {
+            const int ns = p.n_slots[kSolid];
+            for (int a = 0; a < 3; ++a) {
+                p.U0[kSolid][(a * ns + R.slot) * nxp + x] = ce.u[a];
+                p.U0[kSolid][((a + 3) * ns + R.slot) * nxp + x] = cp.u[a];
+            }
+        }
+        const int stride = p.n_rows[kSolid] * nxp, base = it.row * nxp + x;
+        collide_store<Q, T>(ge, ce, je, p.rho0, p.om[1], p.out[1], stride, base);
+        collide_store<Q, T>(gp, cp, jp, p.rho0, p.om[2], p.out[2], stride, base);
+    }
+}
+
+template <int Q, typename T>
+constexpr size_t staged_smem_bytes()
+{
+    return 3 * sizeof(RowInfo) + 2 * (size_t)(2 * Q) * kSeg * sizeof(T);
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlockX, 4) k_step(const StepArgs<T> p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    RowInfo *tab = reinterpret_cast<RowInfo *>(smem);
+    T *stages = reinterpret_cast<T *>(smem + 3 * sizeof(RowInfo));
+    constexpr int kStage = 2 * Q * kSeg;
+    const int G = gridDim.x;
+    int k = blockIdx.x;
+    if (k >= p.snitems) return;
+
+    Item cur = decode_item(p, k);
+    copy_table(p, cur, &tab[0]);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    Item next = cur, after = cur;
+    if (k + G < p.snitems) {
+        next = decode_item(p, k + G);
+        copy_table(p, next, &tab[1]);
+    }
+    issue_item<Q, T>(p, cur, tab[0], stages);
+    cp_async_commit();
+
+    for (int j = 0; k < p.snitems; k += G, ++j) {
+        cp_async_wait_all();
+        __syncthreads();
+        const int kn = k + G;
+        if (kn < p.snitems) {
+            if (kn + G < p.snitems) {
+                after = decode_item(p, kn + G);
+                copy_table(p, after, &tab[(j + 2) % 3]);
+            }
+            issue_item<Q, T>(p, next, tab[(j + 1) % 3], stages + ((j + 1) & 1) * kStage);
+        }
+        cp_async_commit();
+        compute_item<Q, T>(p, cur, tab[j % 3], stages + (j & 1) * kStage);
+        __syncthreads();
+        cur = next;
+        next = after;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
+
+// Persistent grid of the staged step kernel: resident CTAs per SM times SMs,
+// found once per device and instantiation.
+template <int Q, typename T>
+static cudaError_t launch_staged(const StepArgs<T> &a, cudaStream_t s)
+{
+    constexpr size_t smem = staged_smem_bytes<Q, T>();
+    static int grid[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (grid[dev] == 0) {
+        e = cudaFuncSetAttribute(k_step<Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<Q, T>, kBlockX, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        grid[dev] = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    const int nb = a.snitems < grid[dev] ? a.snitems : grid[dev];
+    k_step<Q, T><<<nb, kBlockX, smem, s>>>(a);
+    return cudaGetLastError();
+}
 
 template <int Q, typename T>
 static cudaError_t launch_step_t(const void *args, int mode, int nblocks, int bx, cudaStream_t s)
 {
     const StepArgs<T> &a = *static_cast<const StepArgs<T> *>(args);
-    if (mode == kModeStep)
-        k_lattice<Q, T, kModeStep><<<nblocks, bx, 0, s>>>(a);
-    else if (mode == kModeObserve)
+    if (mode == kModeStep) return launch_staged<Q, T>(a, s);
+    if (mode == kModeObserve)
         k_lattice<Q, T, kModeObserve><<<nblocks, bx, 0, s>>>(a);
     else
         k_lattice<Q, T, kModeField><<<nblocks, bx, 0, s>>>(a);
