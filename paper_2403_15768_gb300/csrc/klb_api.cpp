@@ -85,9 +85,6 @@ void fill_args(const klb_lattice *L, StepArgs<T> &a)
     a.nxp = g.nxp;
     a.nchunk = p.nchunk;
     a.nbw = p.nblocks_w;
-    a.snchunk = (g.nx + kBlockX - 1) / kBlockX;
-    a.snbw = (int)g.rows[kFluid].size() * a.snchunk;
-    a.snitems = a.snbw + (int)g.rows[kSolid].size() * a.snchunk;
     const klb_desc &d = L->desc;
     a.rho0 = (T)d.rho0;
     a.om[0] = (T)(1.0 / d.tau_w);

@@ -102,7 +102,6 @@ struct StepArgs {
     const T *U1[2], *U2[2], *U3[2];  // lagged velocities u(n-1), u(n-2), u(n-3)
     T *U0[2];                        // u(n) written here (step mode)
     int nx, nxp, nchunk, nbw;
-    int snchunk, snbw, snitems;      // staged step: 128-wide x chunks, water items, all items
     int n_rows[2], n_slots[2];
     T rho0, om[3], G[3];
     T g_we, g_wp, g_ep, g_ec, g_pc;

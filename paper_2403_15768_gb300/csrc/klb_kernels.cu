@@ -15,12 +15,13 @@
 // item-uniform.  Water items come first, then the solid items, each of which
 // updates the electrons and phonons of its row.
 //
-// k_step is persistent and stages its sources in shared memory with
-// asynchronous copies.  k_lattice runs the same per-cell arithmetic, loading
-// straight from global memory, for the observation pass (velocities of the
-// current and previous step reduced in FP64) and the field pass.
+// k_step is the lean step kernel.  k_lattice runs the same per-cell
+// arithmetic for the observation pass (velocities of the current and previous
+// step reduced in FP64) and the field pass.
 
 #include <cuda_runtime.h>
+
+#include <cstddef>
 
 #include "klb_internal.h"
 
@@ -520,242 +521,113 @@ __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ par
 }
 
 // ---------------------------------------------------------------------------
-// Staged persistent step kernel.
+// Step kernel.
 //
-// Each CTA walks work items (one row, 128 consecutive x) with a stride of the
-// grid size.  The Q (water) or 2Q (electron + phonon) source-row segments of
-// an item, with one halo element on each side, are copied into shared memory
-// by asynchronous 16-byte copies (cp.async), double-buffered: the next
-// item's copies are in flight while the current item computes, so memory
-// parallelism does not depend on how many threads are resident.  The row
-// table of the item after next is fetched the same way.  Stores go straight
-// to global memory, coalesced along x.
+// One block per work item (one row, up to 128 consecutive x), one cell per
+// thread, no shared memory and no barriers.  Memory parallelism comes from
+// residency: in FP32 the kernel is held to 64 registers (8 blocks of 128
+// threads per SM), and every thread issues its Q (or 2Q) loads back to back.  The row
+// table is read with 16-byte loads (one 128-byte line per row, cached); the x
+// shift of each direction is a compile-time constant except on the few rows
+// where an x-moving population bounces back.  A solid cell streams, and
+// takes the moments of, both its electrons and phonons, then collides and
+// stores the electrons before pulling the phonons a second time (the lines
+// are still cached), so that at most Q populations are live at once.
 
-constexpr int kSegPad = 4;                  // data at element 4: 16-byte aligned
-constexpr int kSeg = kBlockX + 2 * kSegPad;  // elements per staged segment
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(void *smem, const void *gmem)
-{
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-struct Item {
-    int cls, row, x0, n;
-};
-
-template <typename T>
-__device__ __forceinline__ Item decode_item(const StepArgs<T> &p, int k)
-{
-    Item it;
-    it.cls = k < p.snbw ? kFluid : kSolid;
-    const int kk = it.cls == kFluid ? k : k - p.snbw;
-    it.row = kk / p.snchunk;
-    it.x0 = (kk - it.row * p.snchunk) * kBlockX;
-    it.n = min(kBlockX, p.nx - it.x0);
-    return it;
-}
-
-template <typename T>
-__device__ __forceinline__ void copy_table(const StepArgs<T> &p, const Item &it, RowInfo *dst)
-{
-    if (threadIdx.x < sizeof(RowInfo) / 16) {
-        const char *src = reinterpret_cast<const char *>(p.rows[it.cls] + it.row);
-        cp_async16(reinterpret_cast<char *>(dst) + 16 * threadIdx.x, src + 16 * threadIdx.x);
-    }
-}
-
-// Source row (element pointer at x = 0) of staged segment d of an item.
+// Pull-stream the Q populations of one species at x: p0 = x, pm = x - 1 and
+// pp = x + 1 with periodic wrap.
 template <int Q, typename T>
-__device__ __forceinline__ const T *segment_row(const StepArgs<T> &p, const Item &it,
-                                               const RowInfo &R, int d)
+__device__ __forceinline__ void pull_row(const T *__restrict__ in, const int src[Q], uint32_t xm,
+                                         uint32_t xp, bool xbounce, int x, int pm, int pp, T g[Q])
 {
-    const int s = it.cls == kFluid ? 0 : (d < Q ? 1 : 2);
-    const int i = d < Q ? d : d - Q;
-    return p.in[s] + R.src[i];
-}
-
-template <int Q, typename T>
-__device__ __forceinline__ void issue_item(const StepArgs<T> &p, const Item &it, const RowInfo &R,
-                                           T *stage)
-{
-    constexpr int EPC = 16 / sizeof(T);    // elements per 16-byte copy
-    constexpr int L = kBlockX / EPC;       // copy lanes per full segment
-    constexpr int G = kBlockX / L;         // segments per pass of the block
-    const int nseg = it.cls == kFluid ? Q : 2 * Q;
-    const int nfull = it.n / EPC;
-    const int rem = it.n - nfull * EPC;
-    const int t = threadIdx.x;
-    const int c = t % L;
-    if (c < nfull) {
-        for (int d = t / L; d < nseg; d += G)
-            cp_async16(stage + d * kSeg + kSegPad + c * EPC,
-                       segment_row<Q, T>(p, it, R, d) + it.x0 + c * EPC);
-    }
-    // The two periodic halo elements of every segment.
-    const int xl = it.x0 == 0 ? p.nx - 1 : it.x0 - 1;
-    const int xr = it.x0 + it.n == p.nx ? 0 : it.x0 + it.n;
-    for (int f = t; f < 2 * nseg; f += kBlockX) {
-        const int d = f >> 1;
-        const bool right = f & 1;
-        cp_async_small<sizeof(T)>(stage + d * kSeg + (right ? kSegPad + it.n : kSegPad - 1),
-                                  segment_row<Q, T>(p, it, R, d) + (right ? xr : xl));
-    }
-    // Tail elements of a ragged chunk.
-    if (rem) {
-        for (int f = t; f < nseg * rem; f += kBlockX) {
-            const int d = f / rem, e = f - d * rem;
-            cp_async_small<sizeof(T)>(stage + d * kSeg + kSegPad + nfull * EPC + e,
-                                      segment_row<Q, T>(p, it, R, d) + it.x0 + nfull * EPC + e);
-        }
-    }
-}
-
-// Populations of segment group `base` at thread t.  Direction i pulls from
-// x - c_ix except on rows where a direction with c_ix != 0 bounces back
-// (flag kXBounce), whose shifts come from the row's bit masks.
-template <int Q, typename T>
-__device__ __forceinline__ void load_staged(const T *stage, const RowInfo &R, int base, int t,
-                                            T g[Q])
-{
-    const T *s0 = stage + base * kSeg + kSegPad + t;
-    if (!(R.flags & kXBounce)) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = s0[i * kSeg - cx<Q>(i)];
-    } else {
-        const uint32_t xm = R.xm, xp = R.xp;
+    if (!xbounce) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int sh = (int)((xp >> i) & 1u) - (int)((xm >> i) & 1u);
-            g[i] = s0[i * kSeg + sh];
+            const int xs = cx<Q>(i) > 0 ? pm : (cx<Q>(i) < 0 ? pp : x);
+            g[i] = __ldg(in + src[i] + xs);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int xs = ((xm >> i) & 1u) ? pm : (((xp >> i) & 1u) ? pp : x);
+            g[i] = __ldg(in + src[i] + xs);
         }
     }
 }
 
+// The kernel reads the row record as eight 16-byte words.
+static_assert(offsetof(RowInfo, xm) == 19 * 4 && offsetof(RowInfo, xp) == 20 * 4 &&
+                  offsetof(RowInfo, slot) == 21 * 4 && offsetof(RowInfo, flags) == 28 * 4,
+              "row record layout");
+
 template <int Q, typename T>
-__device__ __forceinline__ void compute_item(const StepArgs<T> &p, const Item &it,
-                                             const RowInfo &R, const T *stage)
+__global__ void __launch_bounds__(kBlockX, sizeof(T) == 4 ? 8 : 4) k_step(const StepArgs<T> p)
 {
-    const int t = threadIdx.x;
-    if (t >= it.n) return;
-    const int x = it.x0 + t, nxp = p.nxp;
-    if (it.cls == kFluid) {
+    const int b = blockIdx.x;
+    const bool water = b < p.nbw;
+    const int bb = water ? b : b - p.nbw;
+    const int row = bb / p.nchunk;
+    const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const int pm = x == 0 ? p.nx - 1 : x - 1;
+    const int pp = x == p.nx - 1 ? 0 : x + 1;
+    const int nxp = p.nxp;
+
+    const RowInfo &R = p.rows[water ? kFluid : kSolid][row];
+    const int4 *t4 = reinterpret_cast<const int4 *>(&R);
+    int src[20];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        const int4 q = __ldg(t4 + v);
+        src[4 * v] = q.x;
+        src[4 * v + 1] = q.y;
+        src[4 * v + 2] = q.z;
+        src[4 * v + 3] = q.w;
+    }
+    const uint32_t xm = (uint32_t)src[19];  // the 20th word of a row is its xm mask
+    const int4 q5 = __ldg(t4 + 5);          // xp, slot, nface, partner[0]
+    const int4 q7 = __ldg(t4 + 7);          // flags, pad, pad, pad
+    const uint32_t xp = (uint32_t)q5.x;
+    const bool xbounce = (q7.x & kXBounce) != 0;
+
+    if (water) {
         T g[Q], j[3];
         Cell<T> c;
-        load_staged<Q, T>(stage, R, 0, t, g);
+        pull_row<Q, T>(p.in[0], src, xm, xp, xbounce, x, pm, pp, g);
         water_math<Q, T>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, x, g, c, j);
-        if (R.slot >= 0) {
+        if (q5.y >= 0) {
             const int ns = p.n_slots[kFluid];
-            for (int a = 0; a < 3; ++a) p.U0[kFluid][(a * ns + R.slot) * nxp + x] = c.u[a];
+            for (int a = 0; a < 3; ++a) p.U0[kFluid][(a * ns + q5.y) * nxp + x] = c.u[a];
         }
-        collide_store<Q, T>(g, c, j, p.rho0, p.om[0], p.out[0], p.n_rows[kFluid] * nxp,
-                            it.row * nxp + x);
-    } else {
-        T ge[Q], gp[Q], je[3], jp[3];
-        Cell<T> ce, cp;
-        load_staged<Q, T>(stage, R, 0, t, ge);
-        load_staged<Q, T>(stage, R, Q, t, gp);
-        solid_math<Q, T>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, x, ge, gp,
-                         ce, cp, je, jp);
-        if (R.slot >= 0) {
-            const int ns = p.n_slots[kSolid];
-            for (int a = 0; a < 3; ++a) {
-                p.U0[kSolid][(a * ns + R.slot) * nxp + x] = ce.u[a];
-                p.U0[kSolid][((a + 3) * ns + R.slot) * nxp + x] = cp.u[a];
-            }
+        collide_store<Q, T>(g, c, j, p.rho0, p.om[0], p.out[0], p.n_rows[kFluid] * nxp, row * nxp + x);
+        return;
+    }
+    T ge[Q], gp[Q], je[3], jp[3];
+    Cell<T> ce, cp;
+    pull_row<Q, T>(p.in[1], src, xm, xp, xbounce, x, pm, pp, ge);
+    pull_row<Q, T>(p.in[2], src, xm, xp, xbounce, x, pm, pp, gp);
+    solid_math<Q, T>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, x, ge, gp, ce,
+                     cp, je, jp);
+    if (q5.y >= 0) {
+        const int ns = p.n_slots[kSolid];
+        for (int a = 0; a < 3; ++a) {
+            p.U0[kSolid][(a * ns + q5.y) * nxp + x] = ce.u[a];
+            p.U0[kSolid][((a + 3) * ns + q5.y) * nxp + x] = cp.u[a];
         }
-        const int stride = p.n_rows[kSolid] * nxp, base = it.row * nxp + x;
-        collide_store<Q, T>(ge, ce, je, p.rho0, p.om[1], p.out[1], stride, base);
-        collide_store<Q, T>(gp, cp, jp, p.rho0, p.om[2], p.out[2], stride, base);
     }
-}
-
-template <int Q, typename T>
-constexpr size_t staged_smem_bytes()
-{
-    return 3 * sizeof(RowInfo) + 2 * (size_t)(2 * Q) * kSeg * sizeof(T);
-}
-
-template <int Q, typename T>
-__global__ void __launch_bounds__(kBlockX, 4) k_step(const StepArgs<T> p)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    RowInfo *tab = reinterpret_cast<RowInfo *>(smem);
-    T *stages = reinterpret_cast<T *>(smem + 3 * sizeof(RowInfo));
-    constexpr int kStage = 2 * Q * kSeg;
-    const int G = gridDim.x;
-    int k = blockIdx.x;
-    if (k >= p.snitems) return;
-
-    Item cur = decode_item(p, k);
-    copy_table(p, cur, &tab[0]);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-    Item next = cur, after = cur;
-    if (k + G < p.snitems) {
-        next = decode_item(p, k + G);
-        copy_table(p, next, &tab[1]);
-    }
-    issue_item<Q, T>(p, cur, tab[0], stages);
-    cp_async_commit();
-
-    for (int j = 0; k < p.snitems; k += G, ++j) {
-        cp_async_wait_all();
-        __syncthreads();
-        const int kn = k + G;
-        if (kn < p.snitems) {
-            if (kn + G < p.snitems) {
-                after = decode_item(p, kn + G);
-                copy_table(p, after, &tab[(j + 2) % 3]);
-            }
-            issue_item<Q, T>(p, next, tab[(j + 1) % 3], stages + ((j + 1) & 1) * kStage);
-        }
-        cp_async_commit();
-        compute_item<Q, T>(p, cur, tab[j % 3], stages + (j & 1) * kStage);
-        __syncthreads();
-        cur = next;
-        next = after;
-    }
+    const int stride = p.n_rows[kSolid] * nxp, base = row * nxp + x;
+    collide_store<Q, T>(ge, ce, je, p.rho0, p.om[1], p.out[1], stride, base);
+    pull_row<Q, T>(p.in[2], src, xm, xp, xbounce, x, pm, pp, gp);
+    collide_store<Q, T>(gp, cp, jp, p.rho0, p.om[2], p.out[2], stride, base);
 }
 
 // ---------------------------------------------------------------------------
 // Launchers
 
-// Persistent grid of the staged step kernel: resident CTAs per SM times SMs,
-// found once per device and instantiation.
 template <int Q, typename T>
-static cudaError_t launch_staged(const StepArgs<T> &a, cudaStream_t s)
+static cudaError_t launch_plain_step(const StepArgs<T> &a, int nblocks, int bx, cudaStream_t s)
 {
-    constexpr size_t smem = staged_smem_bytes<Q, T>();
-    static int grid[64] = {0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (grid[dev] == 0) {
-        e = cudaFuncSetAttribute(k_step<Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<Q, T>, kBlockX, smem);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        grid[dev] = (per_sm > 0 ? per_sm : 1) * sms;
-    }
-    const int nb = a.snitems < grid[dev] ? a.snitems : grid[dev];
-    k_step<Q, T><<<nb, kBlockX, smem, s>>>(a);
+    k_step<Q, T><<<nblocks, bx, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -763,7 +635,7 @@ template <int Q, typename T>
 static cudaError_t launch_step_t(const void *args, int mode, int nblocks, int bx, cudaStream_t s)
 {
     const StepArgs<T> &a = *static_cast<const StepArgs<T> *>(args);
-    if (mode == kModeStep) return launch_staged<Q, T>(a, s);
+    if (mode == kModeStep) return launch_plain_step<Q, T>(a, nblocks, bx, s);
     if (mode == kModeObserve)
         k_lattice<Q, T, kModeObserve><<<nblocks, bx, 0, s>>>(a);
     else
