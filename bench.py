@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 LATTICE_STEPS_PER_STEP = 100
-PROFILE = os.path.join(ROOT, "profiles", "k_lattice_step_d3q19_fp32_nanotube_512x128x128.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_step_d3q19_fp32_nanotube_512x128x128.md")
 
 
 def _peaks():
@@ -269,7 +269,7 @@ def run(args):
                    "couplings": list(w.couplings)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _ncu_traffic(),
-                     "kernel": "k_lattice<19,float,step>", "peak_source": peak_kind,
+                     "kernel": "k_step<19,float>", "peak_source": peak_kind,
                      "bytes_per_launch": bytes_per_launch, "launch_ms": step_kernel_ms},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 40,
                 "d2h_bytes_per_step": 144},
