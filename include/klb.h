@@ -50,7 +50,7 @@ typedef enum {
 
 enum { KLB_D2Q9 = 9, KLB_D3Q19 = 19 };
 enum { KLB_GEOM_SLAB = 0, KLB_GEOM_PIPE = 1, KLB_GEOM_MASK = 2 };
-enum { KLB_FP64 = 0, KLB_FP32 = 1 };
+enum { KLB_FP64 = 0, KLB_FP32 = 1, KLB_FP16_DEV = 2, KLB_BF16_DEV = 3 };
 enum { KLB_IFACE_SPECULAR = 0, KLB_IFACE_BOUNCEBACK = 1 };
 enum { KLB_WATER = 0, KLB_ELECTRON = 1, KLB_PHONON = 2 };
 
@@ -71,7 +71,11 @@ enum { KLB_WATER = 0, KLB_ELECTRON = 1, KLB_PHONON = 2 };
  *   rho0    rest density of every species (> 0).
  *   G       uniform body-force density on the water: the pressure drive of
  *           Eq. 2, applied with Guo forcing.
- *   storage KLB_FP64 or KLB_FP32 populations; arithmetic in the same type.
+ *   storage KLB_FP64 or KLB_FP32 populations, arithmetic in the same type;
+ *           or KLB_FP16_DEV / KLB_BF16_DEV: populations stored in 16 bits as
+ *           differences from a per-row FP32 reference population (the row's
+ *           x-average, refreshed every 32 steps; FP16 differences scaled by
+ *           2^20), FP32 arithmetic, FP64 observables.
  *   iface_bc  KLB_IFACE_SPECULAR (free slip at the liquid/solid interface
  *           for all species, Sec. 4.2) or KLB_IFACE_BOUNCEBACK (the Sec. 4.2
  *           alternative); outer solid faces always bounce back.

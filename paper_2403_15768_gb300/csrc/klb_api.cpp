@@ -10,6 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "klb.h"
 #include "klb_internal.h"
 
@@ -26,6 +29,10 @@ struct klb_lattice {
     int64_t step = 0;
     int64_t since_reset = 0;  // steps since creation / init / set_state
     int cur = 0;              // state buffer holding g*(n-1)
+    // Reduced-precision storage: reference generation each state buffer is
+    // encoded with, and whether the next step switches to refreshed references.
+    int gen_buf[2] = {0, 0};
+    bool refresh_pending = false;
     std::string err;
 };
 
@@ -53,7 +60,9 @@ klb_status cuda_fail(klb_lattice *L, cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail((L), e_, #call);  \
     } while (0)
 
-size_t type_size(const klb_lattice *L) { return L->desc.storage == KLB_FP64 ? 8 : 4; }
+size_t pop_size(const klb_lattice *L) { return storage_bytes(L->desc.storage); }
+size_t arith_size(const klb_lattice *L) { return L->desc.storage == KLB_FP64 ? 8 : 4; }
+bool reduced(const klb_lattice *L) { return reduced_storage(L->desc.storage); }
 
 void *dev(const klb_lattice *L, size_t off) { return L->base + off; }
 
@@ -68,9 +77,21 @@ void fill_args(const klb_lattice *L, StepArgs<T> &a)
     std::memset(&a, 0, sizeof a);
     const int n = (int)L->step;  // the step about to run / being observed
     for (int s = 0; s < 3; ++s) {
-        a.in[s] = (const T *)dev(L, p.pop[L->cur][s]);
-        a.out[s] = (T *)dev(L, p.pop[1 - L->cur][s]);
-        a.in_prev[s] = (const T *)dev(L, p.pop[1 - L->cur][s]);
+        a.in[s] = dev(L, p.pop[L->cur][s]);
+        a.out[s] = dev(L, p.pop[1 - L->cur][s]);
+        a.in_prev[s] = dev(L, p.pop[1 - L->cur][s]);
+    }
+    if (reduced(L)) {
+        for (int s = 0; s < 3; ++s) {
+            a.dec_in[s] = (const float *)dev(L, p.ref_dec[L->gen_buf[L->cur]][s]);
+            a.dec_prev[s] = (const float *)dev(L, p.ref_dec[L->gen_buf[1 - L->cur]][s]);
+            a.enc_out[s] = (const float *)dev(L, p.ref_enc[L->gen_buf[L->cur]][s]);
+        }
+        a.scale = L->desc.storage == KLB_FP16_DEV ? kFp16Scale : 1.0f;
+        a.inv_scale = 1.0f / a.scale;
+        a.acc = (float *)dev(L, p.acc);
+    } else {
+        a.scale = a.inv_scale = 1.0f;
     }
     for (int c = 0; c < 2; ++c) {
         a.rows[c] = (const RowInfo *)dev(L, p.rows[c]);
@@ -101,7 +122,7 @@ void fill_args(const klb_lattice *L, StepArgs<T> &a)
     a.field = (T *)dev(L, p.field);
 }
 
-// Runs `body(args, mode-independent)` with typed arguments.
+// Runs `body(args)` with arguments of the lattice's arithmetic type.
 template <typename F>
 cudaError_t with_args(const klb_lattice *L, F body)
 {
@@ -113,6 +134,26 @@ cudaError_t with_args(const klb_lattice *L, F body)
     StepArgs<float> a;
     fill_args(L, a);
     return body(&a);
+}
+
+// Sets the encode references of the next output buffer (generation gen).
+void set_enc(const klb_lattice *L, void *args, int gen)
+{
+    if (!reduced(L)) return;
+    StepArgs<float> *a = static_cast<StepArgs<float> *>(args);
+    for (int s = 0; s < 3; ++s) a->enc_out[s] = (const float *)dev(L, L->plan.ref_enc[gen][s]);
+}
+
+// Reference refresh into generation gen from the x-sums of the last
+// accumulating pass.
+cudaError_t refresh_refs(const klb_lattice *L, int gen)
+{
+    float *enc[3], *dec[3];
+    for (int s = 0; s < 3; ++s) {
+        enc[s] = (float *)dev(L, L->plan.ref_enc[gen][s]);
+        dec[s] = (float *)dev(L, L->plan.ref_dec[gen][s]);
+    }
+    return with_args(L, [&](void *a) { return launch_ref(L->geo.Q, L->desc.storage, a, enc, dec, L->stream); });
 }
 
 int nblocks(const klb_lattice *L) { return L->plan.nblocks_w + L->plan.nblocks_s; }
@@ -166,13 +207,24 @@ klb_status init_from_fields(klb_lattice *L, const double *drho, const double *u)
     L->cur = 0;
     L->step = 0;
     L->since_reset = 0;
+    L->gen_buf[0] = L->gen_buf[1] = 0;
+    L->refresh_pending = false;
     const int slot0 = slot_of(0);
-    KLB_CUDA(L, with_args(L, [&](void *a) {
-                 StepArgs<T> *A = (StepArgs<T> *)a;
-                 for (int s = 0; s < 3; ++s) A->out[s] = (T *)dev(L, L->plan.pop[0][s]);
-                 for (int c = 0; c < 2; ++c) A->U0[c] = (T *)dev(L, L->plan.U[slot0][c]);
-                 return launch_init(L->geo.Q, L->desc.storage, a, nblocks(L), L->plan.bx, L->stream);
-             }));
+    auto init_pass = [&](int mode) {
+        return with_args(L, [&](void *a) {
+            StepArgs<T> *A = (StepArgs<T> *)a;
+            for (int s = 0; s < 3; ++s) A->out[s] = dev(L, L->plan.pop[0][s]);
+            for (int c = 0; c < 2; ++c) A->U0[c] = (T *)dev(L, L->plan.U[slot0][c]);
+            set_enc(L, a, 0);
+            return launch(L->geo.Q, L->desc.storage, a, mode, nblocks(L), L->plan.bx, L->stream);
+        });
+    };
+    if (reduced(L)) {
+        // References first: the x-averages of the initial equilibria.
+        KLB_CUDA(L, init_pass(kModeInitAcc));
+        KLB_CUDA(L, refresh_refs(L, 0));
+    }
+    KLB_CUDA(L, init_pass(kModeInit));
     for (int s = 0; s < 3; ++s)
         KLB_CUDA(L, cudaMemcpyAsync(dev(L, L->plan.pop[1][s]), dev(L, L->plan.pop[0][s]),
                                     L->plan.pop_bytes[s], cudaMemcpyDeviceToDevice, L->stream));
@@ -344,14 +396,27 @@ klb_status klb_step(klb_lattice *L, int64_t nsteps)
     if (!L) return fail(L, KLB_EINVAL, "null handle");
     if (nsteps < 0) return fail(L, KLB_EINVAL, "nsteps must be >= 0");
     for (int64_t n = 0; n < nsteps; ++n) {
+        int outgen = L->gen_buf[L->cur];
+        if (reduced(L) && L->refresh_pending) {
+            // Decode this step with the current references, encode its output
+            // with references refreshed from the last step's x-averages.
+            outgen = 1 - L->gen_buf[L->cur];
+            cudaError_t e = refresh_refs(L, outgen);
+            if (e != cudaSuccess) return cuda_fail(L, e, "reference refresh");
+            L->refresh_pending = false;
+        }
+        const bool acc = reduced(L) && (L->step + 1) % kRefEvery == 0;
         cudaError_t e = with_args(L, [&](void *a) {
-            return launch_step(L->geo.Q, L->desc.storage, a, kModeStep, nblocks(L), L->plan.bx,
-                               L->stream);
+            set_enc(L, a, outgen);
+            return launch(L->geo.Q, L->desc.storage, a, acc ? kModeStepAcc : kModeStep, nblocks(L),
+                          L->plan.bx, L->stream);
         });
         if (e != cudaSuccess) return cuda_fail(L, e, "step kernel launch");
+        L->gen_buf[1 - L->cur] = outgen;
         L->cur = 1 - L->cur;
         ++L->step;
         ++L->since_reset;
+        if (acc) L->refresh_pending = true;
     }
     return KLB_OK;
 }
@@ -360,7 +425,7 @@ klb_status klb_observables(klb_lattice *L, klb_obs *out)
 {
     if (!L || !out) return fail(L, KLB_EINVAL, "null argument");
     KLB_CUDA(L, with_args(L, [&](void *a) {
-                 return launch_step(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L),
+                 return launch(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L),
                                     L->plan.bx, L->stream);
              }));
     KLB_CUDA(L, launch_finalize((const double *)dev(L, L->plan.partials), nblocks(L),
@@ -423,7 +488,7 @@ klb_status klb_observables_static(klb_lattice *L, klb_obs *out)
                      static_cast<StepArgs<double> *>(a)->partials = partials;
                  else
                      static_cast<StepArgs<float> *>(a)->partials = partials;
-                 return launch_step(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L),
+                 return launch(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L),
                                     L->plan.bx, L->stream);
              }));
     KLB_CUDA(L, launch_finalize(partials, nblocks(L), sums, L->stream));
@@ -438,10 +503,10 @@ klb_status klb_get_field(klb_lattice *L, double *drho, double *u)
 {
     if (!L) return fail(L, KLB_EINVAL, "null handle");
     KLB_CUDA(L, with_args(L, [&](void *a) {
-                 return launch_step(L->geo.Q, L->desc.storage, a, kModeField, nblocks(L),
+                 return launch(L->geo.Q, L->desc.storage, a, kModeField, nblocks(L),
                                     L->plan.bx, L->stream);
              }));
-    const size_t ts = type_size(L), nel = L->plan.field_bytes / ts;
+    const size_t ts = arith_size(L), nel = L->plan.field_bytes / ts;
     std::vector<double> f(nel);
     std::vector<char> raw(L->plan.field_bytes);
     KLB_CUDA(L, cudaMemcpyAsync(raw.data(), dev(L, L->plan.field), L->plan.field_bytes,
@@ -473,8 +538,25 @@ klb_status klb_get_state(klb_lattice *L, double *gout, double *U1, double *U2)
 {
     if (!L) return fail(L, KLB_EINVAL, "null handle");
     const Geometry &g = L->geo;
-    const size_t ts = type_size(L), ncell = (size_t)g.nx * g.ny * g.nz, nxp = g.nxp;
+    const size_t ps = pop_size(L), ts = arith_size(L), ncell = (size_t)g.nx * g.ny * g.nz,
+                 nxp = g.nxp;
     const int Q = g.Q;
+    const bool red = reduced(L);
+    const double inv = L->desc.storage == KLB_FP16_DEV ? 1.0 / kFp16Scale : 1.0;
+    // Population value k of a downloaded buffer (reduced storage: the stored
+    // difference, still to be scaled and shifted by its row reference).
+    auto pop = [&](const std::vector<char> &raw, size_t k) -> double {
+        switch (L->desc.storage) {
+        case KLB_FP64:
+            return ((const double *)raw.data())[k];
+        case KLB_FP32:
+            return ((const float *)raw.data())[k];
+        case KLB_FP16_DEV:
+            return (double)__half2float(((const __half *)raw.data())[k]);
+        default:
+            return (double)__bfloat162float(((const __nv_bfloat16 *)raw.data())[k]);
+        }
+    };
     auto rd = [&](const std::vector<char> &raw, size_t k) {
         return ts == 8 ? ((const double *)raw.data())[k] : (double)((const float *)raw.data())[k];
     };
@@ -484,15 +566,25 @@ klb_status klb_get_state(klb_lattice *L, double *gout, double *U1, double *U2)
             std::vector<char> raw(L->plan.pop_bytes[s]);
             KLB_CUDA(L, cudaMemcpyAsync(raw.data(), dev(L, L->plan.pop[L->cur][s]), raw.size(),
                                         cudaMemcpyDeviceToHost, L->stream));
+            std::vector<float> ref;
+            if (red) {
+                ref.resize(L->plan.ref_bytes[s] / sizeof(float));
+                KLB_CUDA(L, cudaMemcpyAsync(ref.data(), dev(L, L->plan.ref_enc[L->gen_buf[L->cur]][s]),
+                                            L->plan.ref_bytes[s], cudaMemcpyDeviceToHost, L->stream));
+            }
             klb_status st = sync(L);
             if (st != KLB_OK) return st;
             const int c = cls_of(s);
             const size_t nr = g.rows[c].size();
             for (int i = 0; i < Q; ++i)
-                for (size_t r = 0; r < nr; ++r)
-                    for (int x = 0; x < g.nx; ++x)
-                        gout[((size_t)s * Q + i) * ncell + x + (size_t)g.nx * g.rows[c][r]] =
-                            rd(raw, (i * nr + r) * nxp + x);
+                for (size_t r = 0; r < nr; ++r) {
+                    const double shift = red ? (double)ref[r * kRefStride + i] : 0.0;
+                    for (int x = 0; x < g.nx; ++x) {
+                        double v = pop(raw, (i * nr + r) * nxp + x);
+                        if (red) v = (double)(float)(v * inv + shift);
+                        gout[((size_t)s * Q + i) * ncell + x + (size_t)g.nx * g.rows[c][r]] = v;
+                    }
+                }
         }
     }
     double *Uo[2] = {U1, U2};
@@ -524,6 +616,7 @@ klb_status klb_get_state(klb_lattice *L, double *gout, double *U1, double *U2)
             }
         }
     }
+    (void)ps;
     return KLB_OK;
 }
 
@@ -533,8 +626,26 @@ klb_status klb_set_state(klb_lattice *L, const double *gin, const double *U1, co
     if (!L || !gin || !U1 || !U2) return fail(L, KLB_EINVAL, "null argument");
     if (step < 0) return fail(L, KLB_EINVAL, "step must be >= 0");
     const Geometry &g = L->geo;
-    const size_t ts = type_size(L), ncell = (size_t)g.nx * g.ny * g.nz, nxp = g.nxp;
+    const size_t ts = arith_size(L), ncell = (size_t)g.nx * g.ny * g.nz, nxp = g.nxp;
     const int Q = g.Q;
+    const bool red = reduced(L);
+    const double scale = L->desc.storage == KLB_FP16_DEV ? kFp16Scale : 1.0;
+    auto put = [&](std::vector<char> &raw, size_t k, double v) {
+        switch (L->desc.storage) {
+        case KLB_FP64:
+            ((double *)raw.data())[k] = v;
+            break;
+        case KLB_FP32:
+            ((float *)raw.data())[k] = (float)v;
+            break;
+        case KLB_FP16_DEV:
+            ((__half *)raw.data())[k] = __float2half_rn((float)v);
+            break;
+        default:
+            ((__nv_bfloat16 *)raw.data())[k] = __float2bfloat16_rn((float)v);
+            break;
+        }
+    };
     auto wr = [&](std::vector<char> &raw, size_t k, double v) {
         if (ts == 8)
             ((double *)raw.data())[k] = v;
@@ -545,18 +656,52 @@ klb_status klb_set_state(klb_lattice *L, const double *gin, const double *U1, co
     L->cur = 0;
     L->step = step;
     L->since_reset = 0;
+    L->gen_buf[0] = L->gen_buf[1] = 0;
+    L->refresh_pending = false;
+    std::vector<float> enc[3];
     for (int s = 0; s < 3; ++s) {
-        std::vector<char> raw(L->plan.pop_bytes[s], 0);
         const int c = cls_of(s);
         const size_t nr = g.rows[c].size();
+        if (red) {
+            // Reference of each (row, direction): the x-average of the state.
+            enc[s].assign(nr * kRefStride, 0.f);
+            for (int i = 0; i < Q; ++i)
+                for (size_t r = 0; r < nr; ++r) {
+                    double sum = 0.0;
+                    for (int x = 0; x < g.nx; ++x)
+                        sum += gin[((size_t)s * Q + i) * ncell + x + (size_t)g.nx * g.rows[c][r]];
+                    enc[s][r * kRefStride + i] = (float)(sum / g.nx);
+                }
+        }
+        std::vector<char> raw(L->plan.pop_bytes[s], 0);
         for (int i = 0; i < Q; ++i)
-            for (size_t r = 0; r < nr; ++r)
-                for (int x = 0; x < g.nx; ++x)
-                    wr(raw, (i * nr + r) * nxp + x,
-                       gin[((size_t)s * Q + i) * ncell + x + (size_t)g.nx * g.rows[c][r]]);
+            for (size_t r = 0; r < nr; ++r) {
+                const float ref = red ? enc[s][r * kRefStride + i] : 0.f;
+                for (int x = 0; x < g.nx; ++x) {
+                    const double v = gin[((size_t)s * Q + i) * ncell + x + (size_t)g.nx * g.rows[c][r]];
+                    put(raw, (i * nr + r) * nxp + x, red ? ((float)v - ref) * (float)scale : v);
+                }
+            }
         for (int b = 0; b < 2; ++b)
             KLB_CUDA(L, cudaMemcpy(dev(L, L->plan.pop[b][s]), raw.data(), raw.size(),
                                    cudaMemcpyHostToDevice));
+    }
+    if (red) {
+        for (int s = 0; s < 3; ++s) {
+            const int c = cls_of(s);
+            const size_t nr = g.rows[c].size();
+            std::vector<float> dec(nr * kRefStride, 0.f);
+            for (size_t r = 0; r < nr; ++r)
+                for (int i = 0; i < Q; ++i) {
+                    const long q = g.info[c][r].src[i] / g.nxp;  // sdir * nr + srow
+                    const long sdir = q / (long)nr, srow = q - sdir * (long)nr;
+                    dec[r * kRefStride + i] = enc[s][srow * kRefStride + sdir];
+                }
+            KLB_CUDA(L, cudaMemcpy(dev(L, L->plan.ref_enc[0][s]), enc[s].data(), L->plan.ref_bytes[s],
+                                   cudaMemcpyHostToDevice));
+            KLB_CUDA(L, cudaMemcpy(dev(L, L->plan.ref_dec[0][s]), dec.data(), L->plan.ref_bytes[s],
+                                   cudaMemcpyHostToDevice));
+        }
     }
     const double *Ui[3] = {U1, U2, U2};  // u(n-1), u(n-2); u(n-3) unknown: reuse u(n-2)
     for (int t = 0; t < 3; ++t) {

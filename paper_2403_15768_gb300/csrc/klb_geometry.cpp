@@ -92,7 +92,8 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
     if (d.kind != KLB_D2Q9 && d.kind != KLB_D3Q19) return err = "kind must be KLB_D2Q9 or KLB_D3Q19", false;
     if (d.nx < 1 || d.ny < 1 || d.nz < 1) return err = "nx, ny, nz must be >= 1", false;
     if (d.kind == KLB_D2Q9 && d.nz != 1) return err = "D2Q9 needs nz == 1", false;
-    if (d.storage != KLB_FP64 && d.storage != KLB_FP32) return err = "storage must be KLB_FP64 or KLB_FP32", false;
+    if (d.storage != KLB_FP64 && d.storage != KLB_FP32 && !reduced_storage(d.storage))
+        return err = "storage must be KLB_FP64, KLB_FP32, KLB_FP16_DEV or KLB_BF16_DEV", false;
     if (d.iface_bc != KLB_IFACE_SPECULAR && d.iface_bc != KLB_IFACE_BOUNCEBACK)
         return err = "iface_bc must be SPECULAR or BOUNCEBACK", false;
     double taus[3] = {d.tau_w, d.tau_e, d.tau_p};
@@ -288,7 +289,8 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
 MemoryPlan plan_memory(const Geometry &g, int storage)
 {
     MemoryPlan p;
-    const size_t ts = storage == KLB_FP64 ? 8 : 4;
+    const size_t ss = storage_bytes(storage);            // population storage
+    const size_t ts = storage == KLB_FP64 ? 8 : 4;       // arithmetic type
     const size_t nr[2] = {g.rows[kFluid].size(), g.rows[kSolid].size()};
     const size_t ns[2] = {g.slot_row[kFluid].size(), g.slot_row[kSolid].size()};
     size_t off = 0;
@@ -297,7 +299,7 @@ MemoryPlan plan_memory(const Geometry &g, int storage)
         off += (bytes + 255) / 256 * 256;
         return at;
     };
-    for (int s = 0; s < 3; ++s) p.pop_bytes[s] = ts * g.Q * nr[s == 0 ? kFluid : kSolid] * g.nxp;
+    for (int s = 0; s < 3; ++s) p.pop_bytes[s] = ss * g.Q * nr[s == 0 ? kFluid : kSolid] * g.nxp;
     for (int b = 0; b < 2; ++b)
         for (int s = 0; s < 3; ++s) p.pop[b][s] = take(p.pop_bytes[s]);
     p.U_bytes[kFluid] = ts * 3 * ns[kFluid] * g.nxp;
@@ -314,6 +316,21 @@ MemoryPlan plan_memory(const Geometry &g, int storage)
     p.sums = take(sizeof(double) * kNumSums);
     p.field_bytes = ts * 4 * (nr[kFluid] + 2 * nr[kSolid]) * g.nxp;
     p.field = take(p.field_bytes);
+    for (int s = 0; s < 3; ++s) p.ref_bytes[s] = 0;
+    p.acc = p.acc_bytes = 0;
+    for (int gen = 0; gen < 2; ++gen)
+        for (int s = 0; s < 3; ++s) p.ref_enc[gen][s] = p.ref_dec[gen][s] = 0;
+    if (reduced_storage(storage)) {
+        for (int s = 0; s < 3; ++s)
+            p.ref_bytes[s] = sizeof(float) * kRefStride * nr[s == 0 ? kFluid : kSolid];
+        for (int gen = 0; gen < 2; ++gen)
+            for (int s = 0; s < 3; ++s) {
+                p.ref_enc[gen][s] = take(p.ref_bytes[s]);
+                p.ref_dec[gen][s] = take(p.ref_bytes[s]);
+            }
+        p.acc_bytes = sizeof(float) * 2 * g.Q * (size_t)(p.nblocks_w + p.nblocks_s);
+        p.acc = take(p.acc_bytes);
+    }
     p.total = off;
     return p;
 }

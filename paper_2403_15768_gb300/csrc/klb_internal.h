@@ -87,17 +87,35 @@ struct MemoryPlan {
     size_t rows[2];
     size_t partials, sums, field;
     size_t field_bytes;
+    size_t ref_enc[2][3], ref_dec[2][3];  // [generation][species], reduced storage only
+    size_t ref_bytes[3];
+    size_t acc, acc_bytes;
     size_t total;
     int nblocks_w, nblocks_s, nchunk, bx;
 };
 MemoryPlan plan_memory(const Geometry &g, int storage);
 
-// Kernel arguments.  T is the storage and arithmetic type (float or double).
+// Reduced-precision storage: floats per row in the reference tables (Q
+// used, padded to a multiple of four), steps between reference refreshes,
+// and the power-of-two scale of FP16 differences (keeps them out of the
+// subnormal range).
+constexpr int kRefStride = 20;
+constexpr int kRefEvery = 32;
+constexpr float kFp16Scale = 1048576.0f;  // 2^20
+
+inline bool reduced_storage(int storage) { return storage == KLB_FP16_DEV || storage == KLB_BF16_DEV; }
+inline size_t storage_bytes(int storage)
+{
+    return storage == KLB_FP64 ? 8 : (storage == KLB_FP32 ? 4 : 2);
+}
+
+// Kernel arguments.  T is the arithmetic type (float or double); the
+// populations are stored as T, or as FP16/BF16 against per-row references.
 template <typename T>
 struct StepArgs {
-    const T *in[3];        // current state, per species
-    T *out[3];             // next state (step mode)
-    const T *in_prev[3];   // previous state (observe mode, residual)
+    const void *in[3];     // current state, per species
+    void *out[3];          // next state (step and init modes)
+    const void *in_prev[3];  // previous state (observe mode, residual)
     const RowInfo *rows[2];
     const T *U1[2], *U2[2], *U3[2];  // lagged velocities u(n-1), u(n-2), u(n-3)
     T *U0[2];                        // u(n) written here (step mode)
@@ -108,15 +126,28 @@ struct StepArgs {
     double *partials;      // observe mode: [block][kNumSums]
     int residual_valid;
     T *field;              // field / init mode: per species [4][n_rows][nxp]
+    // reduced-precision storage only (null otherwise)
+    const float *dec_in[3], *dec_prev[3];  // references of pulled populations
+    const float *enc_out[3];               // references of stored populations
+    float scale, inv_scale;
+    float *acc;            // per-block x-sums of g* [block][2Q]
 };
 
-enum Mode { kModeStep = 0, kModeObserve = 1, kModeField = 2 };
+enum Mode {
+    kModeStep = 0,
+    kModeObserve = 1,
+    kModeField = 2,
+    kModeStepAcc = 3,  // step that also writes the x-sums for a refresh
+    kModeInit = 4,
+    kModeInitAcc = 5   // x-sums of the initial equilibria, nothing stored
+};
 
 // Launchers (return the launch error, if any).
-cudaError_t launch_step(int Q, int storage, const void *args, int mode, int nblocks, int bx,
-                        cudaStream_t s);
-cudaError_t launch_init(int Q, int storage, const void *args, int nblocks, int bx,
-                        cudaStream_t s);
+cudaError_t launch(int Q, int storage, const void *args, int mode, int nblocks, int bx,
+                   cudaStream_t s);
+// Reference refresh from args.acc into the tables enc[s], dec[s].
+cudaError_t launch_ref(int Q, int storage, const void *args, float *const enc[3],
+                       float *const dec[3], cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s);
 
 // Static scratch of klb_observables_static (klb_static.cu): device addresses

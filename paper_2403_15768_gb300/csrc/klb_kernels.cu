@@ -1,498 +1,28 @@
-// CUDA kernels of the KLB step for sm_103a.
-//
-// One fused kernel per lattice step (k_step) updates all three species
-// (Sec. 4: one population set per species, {h_i, e_i, p_i}):
-//   pull-stream (boundary rules of Sec. 4.2, precomputed per row) ->
-//   moments -> interface friction (Eq. 27) from lagged velocities ->
-//   trapezoidal electron-phonon friction and crystal sinks (Eqs. 12, 13, 16) ->
-//   Guo velocity -> BGK collision with Guo forcing (body force of Eq. 2) ->
-//   store (A-B: the state is read from one buffer and written to the other).
-//
-// Layout: structure of arrays, per species [direction][row][x] with rows of
-// nxp elements (x fastest, rows padded to 32 elements), so every copy and
-// store of a warp is a contiguous run of x.  A work item is 128 consecutive
-// x of one row; the row table (sources, x shifts, interface partners) is
-// item-uniform.  Water items come first, then the solid items, each of which
-// updates the electrons and phonons of its row.
-//
-// k_step is the lean step kernel.  k_lattice runs the same per-cell
-// arithmetic for the observation pass (velocities of the current and previous
-// step reduced in FP64) and the field pass.
+// Kernel dispatch by lattice and the final reduction of the observation sums.
 
 #include <cuda_runtime.h>
-
-#include <cstddef>
 
 #include "klb_internal.h"
 
 namespace klb {
 
-// ---------------------------------------------------------------------------
-// Lattice constants, folded at compile time inside unrolled loops.
+cudaError_t launch_q9(int storage, const void *args, int mode, int nblocks, int bx, cudaStream_t s);
+cudaError_t launch_q19(int storage, const void *args, int mode, int nblocks, int bx, cudaStream_t s);
+cudaError_t launch_ref_q9(const void *args, float *const enc[3], float *const dec[3], cudaStream_t s);
+cudaError_t launch_ref_q19(const void *args, float *const enc[3], float *const dec[3], cudaStream_t s);
 
-template <int Q> __host__ __device__ constexpr int cx(int i);
-template <int Q> __host__ __device__ constexpr int cy(int i);
-template <int Q> __host__ __device__ constexpr int cz(int i);
-template <int Q> __host__ __device__ constexpr double wt(int i);
-
-template <> __host__ __device__ constexpr int cx<9>(int i)
+cudaError_t launch(int Q, int storage, const void *args, int mode, int nblocks, int bx,
+                   cudaStream_t s)
 {
-    return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
-}
-template <> __host__ __device__ constexpr int cy<9>(int i)
-{
-    return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
-}
-template <> __host__ __device__ constexpr int cz<9>(int) { return 0; }
-template <> __host__ __device__ constexpr double wt<9>(int i)
-{
-    return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    return Q == 9 ? launch_q9(storage, args, mode, nblocks, bx, s)
+                  : launch_q19(storage, args, mode, nblocks, bx, s);
 }
 
-// D3Q19: 0 rest; 1..6 (+x,-x,+y,-y,+z,-z); 7..18 edges in opposite pairs.
-__host__ __device__ constexpr int c19(int i, int a)
+cudaError_t launch_ref(int Q, int storage, const void *args, float *const enc[3],
+                       float *const dec[3], cudaStream_t s)
 {
-    constexpr int t[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
-                              {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
-                              {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                              {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-    return t[i][a];
-}
-template <> __host__ __device__ constexpr int cx<19>(int i) { return c19(i, 0); }
-template <> __host__ __device__ constexpr int cy<19>(int i) { return c19(i, 1); }
-template <> __host__ __device__ constexpr int cz<19>(int i) { return c19(i, 2); }
-template <> __host__ __device__ constexpr double wt<19>(int i)
-{
-    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-}
-
-// ---------------------------------------------------------------------------
-
-template <typename T>
-struct Cell {
-    T drho;   // density deviation
-    T u[3];   // Guo velocity (j + F/2) / rho
-    T F[3];   // total force density
-};
-
-// Pull-stream the Q populations of one species at (row, x).
-template <int Q, typename T>
-__device__ __forceinline__ void pull(const T *__restrict__ in, const RowInfo &R, int x, int xm1,
-                                     int xp1, T g[Q])
-{
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int xs = ((R.xm >> i) & 1u) ? xm1 : (((R.xp >> i) & 1u) ? xp1 : x);
-        g[i] = __ldg(in + R.src[i] + xs);
-    }
-}
-
-// c_i . v with only the non-zero velocity components (no additions of 0,
-// which IEEE signed zeros keep the compiler from dropping).
-template <int Q, typename T>
-__device__ __forceinline__ T cdot(int i, const T v[3])
-{
-    const int c[3] = {cx<Q>(i), cy<Q>(i), cz<Q>(i)};
-    T r = T(0);
-    bool any = false;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (c[a] == 0) continue;
-        if (!any)
-            r = c[a] > 0 ? v[a] : -v[a];
-        else
-            r = c[a] > 0 ? r + v[a] : r - v[a];
-        any = true;
-    }
-    return r;
-}
-
-// Sum of +-g_i over the directions with c_ia = +-1 (first term not added to 0).
-template <int Q, typename T>
-__device__ __forceinline__ T cmoment(int a, const T g[Q])
-{
-    T r = T(0);
-    bool any = false;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int c = a == 0 ? cx<Q>(i) : (a == 1 ? cy<Q>(i) : cz<Q>(i));
-        if (c == 0) continue;
-        if (!any)
-            r = c > 0 ? g[i] : -g[i];
-        else
-            r = c > 0 ? r + g[i] : r - g[i];
-        any = true;
-    }
-    return r;
-}
-
-template <int Q, typename T>
-__device__ __forceinline__ void moments(const T g[Q], T &drho, T j[3])
-{
-    drho = g[0];
-#pragma unroll
-    for (int i = 1; i < Q; ++i) drho += g[i];
-    j[0] = cmoment<Q, T>(0, g);
-    j[1] = cmoment<Q, T>(1, g);
-    j[2] = Q == 19 ? cmoment<Q, T>(2, g) : T(0);
-}
-
-// Index of the direction with velocity (a, b, c), at compile time.
-template <int Q>
-__host__ __device__ constexpr int dir_index(int a, int b, int c)
-{
-    int k = -1;
-    for (int i = 0; i < Q; ++i)
-        if (cx<Q>(i) == a && cy<Q>(i) == b && cz<Q>(i) == c) k = i;
-    return k;
-}
-
-// BGK with Guo forcing, deviation form:
-// g*_i = g_i + om (geq_i - g_i) + (1 - om/2) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F,
-// geq_i = w_i [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)].
-// The exact scheme conserves mass and gives post-collision momentum j + F.
-// In FP32 the lattice weights (1/18, 1/36, ...) are not representable, and
-// the rounded weights bias both moments by the same relative amount in every
-// cell and every step, a drift that accumulates over the slow relaxation of
-// the channel flow.  FP32 therefore restores the two moments after the
-// collision: the mass residual goes to the rest population, the momentum
-// residual of each axis to its pair of axis populations.  The remaining
-// rounding is unbiased.
-template <int Q, typename T>
-__device__ __forceinline__ void collide_store(T g[Q], const Cell<T> &c, const T j[3], T rho0,
-                                              T om, T *__restrict__ out, int row_stride, int base)
-{
-    const T rho = rho0 + c.drho;
-    const T uu = c.u[0] * c.u[0] + c.u[1] * c.u[1] + c.u[2] * c.u[2];
-    const T uF = c.u[0] * c.F[0] + c.u[1] * c.F[1] + c.u[2] * c.F[2];
-    const T e0 = c.drho - T(1.5) * rho * uu;
-    const T r3 = T(3) * rho, r45 = T(4.5) * rho;
-    const T m3uF = T(-3) * uF;
-    const T om1 = T(1) - om;
-    const T fo = T(1) - T(0.5) * om;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const T w = T(wt<Q>(i));
-        if (i == 0) {  // rest population: c = 0
-            g[0] = om1 * g[0] + (om * w) * e0 + (fo * w) * m3uF;
-            continue;
-        }
-        const T cu = cdot<Q, T>(i, c.u);
-        const T cF = cdot<Q, T>(i, c.F);
-        const T teq = e0 + cu * (r3 + r45 * cu);
-        const T tF = m3uF + cF * (T(3) + T(9) * cu);
-        g[i] = om1 * g[i] + (om * w) * teq + (fo * w) * tF;
-    }
-    if (sizeof(T) == 4) {
-        T m = g[0];
-#pragma unroll
-        for (int i = 1; i < Q; ++i) m += g[i];
-        const T p[3] = {cmoment<Q, T>(0, g), cmoment<Q, T>(1, g),
-                        Q == 19 ? cmoment<Q, T>(2, g) : T(0)};
-        g[0] += c.drho - m;
-        const T hx = T(0.5) * ((j[0] + c.F[0]) - p[0]);
-        const T hy = T(0.5) * ((j[1] + c.F[1]) - p[1]);
-        g[dir_index<Q>(1, 0, 0)] += hx;
-        g[dir_index<Q>(-1, 0, 0)] -= hx;
-        g[dir_index<Q>(0, 1, 0)] += hy;
-        g[dir_index<Q>(0, -1, 0)] -= hy;
-        if (Q == 19) {
-            const T hz = T(0.5) * ((j[2] + c.F[2]) - p[2]);
-            g[dir_index<Q>(0, 0, 1)] += hz;
-            g[dir_index<Q>(0, 0, -1)] -= hz;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) out[i * row_stride + base] = g[i];
-}
-
-template <typename T>
-__device__ __forceinline__ T lagged(const T *U1, const T *U2, int idx)
-{
-    return T(0.5) * (U1[idx] + U2[idx]);
-}
-
-// Water cell given its streamed populations g: moments, interface friction,
-// Guo velocity.  U1/U2 are the velocities of the two steps before the time
-// level of g; R is the row's table (global or shared memory).
-template <int Q, typename T>
-__device__ __forceinline__ void water_math(const StepArgs<T> &p, const T *Uw1, const T *Uw2,
-                                           const T *Us1, const T *Us2, const RowInfo &R, int x,
-                                           const T g[Q], Cell<T> &c, T j[3])
-{
-    moments<Q, T>(g, c.drho, j);
-    c.F[0] = p.G[0];
-    c.F[1] = p.G[1];
-    c.F[2] = p.G[2];
-    const int slot = R.slot;
-    if (slot >= 0) {
-        const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
-        const int nface = R.nface;
-        for (int a = 0; a < 3; ++a) {
-            const T uw = lagged(Uw1, Uw2, (a * ns_w + slot) * nxp + x);
-            T f = T(0);
-            for (int k = 0; k < nface; ++k) {
-                const int q = R.partner[k];
-                const T de = uw - lagged(Us1, Us2, (a * ns_s + q) * nxp + x);
-                const T dp = uw - lagged(Us1, Us2, ((a + 3) * ns_s + q) * nxp + x);
-                f -= p.g_we * de + p.g_wp * dp;
-            }
-            c.F[a] += f;
-        }
-    }
-    const T rinv = T(1) / (p.rho0 + c.drho);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) c.u[a] = (j[a] + T(0.5) * c.F[a]) * rinv;
-}
-
-template <int Q, typename T>
-__device__ __forceinline__ void water_cell(const StepArgs<T> &p, const T *__restrict__ in,
-                                           const T *Uw1, const T *Uw2, const T *Us1,
-                                           const T *Us2, const RowInfo &R, int x, int xm1,
-                                           int xp1, T g[Q], Cell<T> &c, T j[3])
-{
-    pull<Q, T>(in, R, x, xm1, xp1, g);
-    water_math<Q, T>(p, Uw1, Uw2, Us1, Us2, R, x, g, c, j);
-}
-
-// Electrons and phonons of one solid cell given their streamed populations.
-template <int Q, typename T>
-__device__ __forceinline__ void solid_math(const StepArgs<T> &p, const T *Uw1, const T *Uw2,
-                                           const T *Us1, const T *Us2, const RowInfo &R, int x,
-                                           const T ge[Q], const T gp[Q], Cell<T> &ce,
-                                           Cell<T> &cp, T je[3], T jp[3])
-{
-    moments<Q, T>(ge, ce.drho, je);
-    moments<Q, T>(gp, cp.drho, jp);
-    T Fe[3] = {T(0), T(0), T(0)}, Fp[3] = {T(0), T(0), T(0)};
-    const int slot = R.slot;
-    if (slot >= 0) {
-        const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
-        const int nface = R.nface;
-        for (int a = 0; a < 3; ++a) {
-            const T ue = lagged(Us1, Us2, (a * ns_s + slot) * nxp + x);
-            const T up = lagged(Us1, Us2, ((a + 3) * ns_s + slot) * nxp + x);
-            T fe = T(0), fp = T(0);
-            for (int k = 0; k < nface; ++k) {
-                const T uw = lagged(Uw1, Uw2, (a * ns_w + R.partner[k]) * nxp + x);
-                fe += p.g_we * (uw - ue);
-                fp += p.g_wp * (uw - up);
-            }
-            Fe[a] = fe;
-            Fp[a] = fp;
-        }
-    }
-    // Trapezoidal e-p friction and sinks, solved exactly per component:
-    // (a + k + se) ue - k up = Je,  -k ue + (b + k + sp) up = Jp.
-    const T ra = p.rho0 + ce.drho, rb = p.rho0 + cp.drho;
-    const T k = T(0.5) * p.g_ep, se = T(0.5) * p.g_ec, sp = T(0.5) * p.g_pc;
-    const T A = ra + k + se, B = rb + k + sp;
-    const T Dinv = T(1) / (A * B - k * k);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const T Je = je[a] + T(0.5) * Fe[a];
-        const T Jp = jp[a] + T(0.5) * Fp[a];
-        const T ue = (B * Je + k * Jp) * Dinv;
-        const T up = (A * Jp + k * Je) * Dinv;
-        ce.u[a] = ue;
-        cp.u[a] = up;
-        ce.F[a] = Fe[a] - p.g_ep * (ue - up) - p.g_ec * ue;
-        cp.F[a] = Fp[a] + p.g_ep * (ue - up) - p.g_pc * up;
-    }
-}
-
-template <int Q, typename T>
-__device__ __forceinline__ void solid_cell(const StepArgs<T> &p, const T *__restrict__ in_e,
-                                           const T *__restrict__ in_p, const T *Uw1,
-                                           const T *Uw2, const T *Us1, const T *Us2,
-                                           const RowInfo &R, int x, int xm1, int xp1, T ge[Q],
-                                           T gp[Q], Cell<T> &ce, Cell<T> &cp, T je[3], T jp[3])
-{
-    pull<Q, T>(in_e, R, x, xm1, xp1, ge);
-    pull<Q, T>(in_p, R, x, xm1, xp1, gp);
-    solid_math<Q, T>(p, Uw1, Uw2, Us1, Us2, R, x, ge, gp, ce, cp, je, jp);
-}
-
-// ---------------------------------------------------------------------------
-// Block reduction of the observation sums (FP64, fixed order).
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-__device__ void block_reduce_store(double (&s)[kNumSums], double *out)
-{
-    __shared__ double red[kNumSums][kBlockX / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < kNumSums; ++k) {
-        double v = (k == kSumResidual) ? warp_max(s[k]) : warp_sum(s[k]);
-        if (lane == 0) red[k][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kNumSums) {
-        const int k = threadIdx.x;
-        double v = red[k][0];
-        for (int w = 1; w < nwarps; ++w) v = (k == kSumResidual) ? fmax(v, red[k][w]) : v + red[k][w];
-        out[k] = v;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ bool finite3(const Cell<T> &c)
-{
-    return isfinite((double)c.drho) && isfinite((double)c.u[0]) && isfinite((double)c.u[1]) &&
-           isfinite((double)c.u[2]);
-}
-
-// ---------------------------------------------------------------------------
-
-template <int Q, typename T, int MODE>
-__global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
-{
-    const int b = blockIdx.x;
-    const bool water = b < p.nbw;
-    const int bb = water ? b : b - p.nbw;
-    const int row = bb / p.nchunk;
-    const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
-    const bool live = x < p.nx;
-
-    double s[kNumSums];
-    if (MODE == kModeObserve) {
-#pragma unroll
-        for (int k = 0; k < kNumSums; ++k) s[k] = 0.0;
-    }
-
-    if (live) {
-        const int xm1 = x == 0 ? p.nx - 1 : x - 1;
-        const int xp1 = x == p.nx - 1 ? 0 : x + 1;
-        const int nxp = p.nxp;
-        if (water) {
-            const RowInfo &R = p.rows[kFluid][row];
-            T g[Q], j[3];
-            Cell<T> c;
-            water_cell<Q, T>(p, p.in[0], p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R,
-                             x, xm1, xp1, g, c, j);
-            if (MODE == kModeField) {
-                T *f = p.field;
-                f[row * nxp + x] = c.drho;
-                for (int a = 0; a < 3; ++a) f[((a + 1) * p.n_rows[kFluid] + row) * nxp + x] = c.u[a];
-            } else {
-                const double ux = (double)c.u[0];
-                const double rho = (double)(p.rho0 + c.drho);
-                s[kSumUxFluid] = ux;
-                s[kSumMomW] = rho * ux;
-                s[kSumMassW] = (double)c.drho;
-                s[kSumNonfinite] = finite3(c) ? 0.0 : 1.0;
-                if (R.flags & kFitRow) {
-                    const double d2 = (double)R.d2;
-                    s[kSumFitN] = 1.0;
-                    s[kSumFitD2] = d2;
-                    s[kSumFitD4] = d2 * d2;
-                    s[kSumFitU] = ux;
-                    s[kSumFitUD2] = ux * d2;
-                }
-                if (R.flags & kWallRow) {
-                    s[kSumWallN] = 1.0;
-                    s[kSumWallU] = ux;
-                }
-                if (p.residual_valid) {
-                    Cell<T> cprev;
-                    water_cell<Q, T>(p, p.in_prev[0], p.U2[kFluid], p.U3[kFluid], p.U2[kSolid],
-                                     p.U3[kSolid], R, x, xm1, xp1, g, cprev, j);
-                    s[kSumResidual] = fabs(ux - (double)cprev.u[0]);
-                }
-            }
-        } else {
-            const RowInfo &R = p.rows[kSolid][row];
-            T ge[Q], gp[Q], je[3], jp[3];
-            Cell<T> ce, cp;
-            solid_cell<Q, T>(p, p.in[1], p.in[2], p.U1[kFluid], p.U2[kFluid], p.U1[kSolid],
-                             p.U2[kSolid], R, x, xm1, xp1, ge, gp, ce, cp, je, jp);
-            if (MODE == kModeField) {
-                const int nrw = p.n_rows[kFluid], nrs = p.n_rows[kSolid];
-                T *fe = p.field + (size_t)4 * nrw * nxp;
-                T *fp = fe + (size_t)4 * nrs * nxp;
-                fe[(0 * nrs + row) * nxp + x] = ce.drho;
-                fp[(0 * nrs + row) * nxp + x] = cp.drho;
-                for (int a = 0; a < 3; ++a) {
-                    fe[((a + 1) * nrs + row) * nxp + x] = ce.u[a];
-                    fp[((a + 1) * nrs + row) * nxp + x] = cp.u[a];
-                }
-            } else {
-                const double ue = (double)ce.u[0], up = (double)cp.u[0];
-                s[kSumUxE] = ue;
-                s[kSumUxP] = up;
-                s[kSumMomE] = (double)(p.rho0 + ce.drho) * ue;
-                s[kSumMomP] = (double)(p.rho0 + cp.drho) * up;
-                s[kSumMassE] = (double)ce.drho;
-                s[kSumMassP] = (double)cp.drho;
-                s[kSumNonfinite] = (finite3(ce) ? 0.0 : 1.0) + (finite3(cp) ? 0.0 : 1.0);
-                if (p.residual_valid) {
-                    Cell<T> pe, pp;
-                    solid_cell<Q, T>(p, p.in_prev[1], p.in_prev[2], p.U2[kFluid], p.U3[kFluid],
-                                     p.U2[kSolid], p.U3[kSolid], R, x, xm1, xp1, ge, gp, pe, pp, je,
-                                     jp);
-                    s[kSumResidual] = fmax(fabs(ue - (double)pe.u[0]), fabs(up - (double)pp.u[0]));
-                }
-            }
-        }
-    }
-    if (MODE == kModeObserve) block_reduce_store(s, p.partials + (size_t)b * kNumSums);
-}
-
-// Start from the local equilibrium of the fields (drho, u) staged in p.field
-// (the layout the field pass writes): the state buffer p.out and the
-// lagged-velocity slot p.U0 are filled; the host copies them to the others.
-template <int Q, typename T>
-__global__ void __launch_bounds__(kBlockX) k_init(const StepArgs<T> p)
-{
-    const int b = blockIdx.x;
-    const bool water = b < p.nbw;
-    const int bb = water ? b : b - p.nbw;
-    const int row = bb / p.nchunk;
-    const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const int nxp = p.nxp;
-    const int nrw = p.n_rows[kFluid], nrs = p.n_rows[kSolid];
-    const int cls = water ? kFluid : kSolid;
-    const RowInfo &R = p.rows[cls][row];
-    const int nsp = water ? 1 : 2;
-    for (int k = 0; k < nsp; ++k) {
-        const int s = water ? 0 : 1 + k;
-        const int nr = water ? nrw : nrs;
-        const T *f = p.field;
-        if (s >= 1) f += (size_t)4 * nrw * nxp;
-        if (s == 2) f += (size_t)4 * nrs * nxp;
-        Cell<T> c;
-        c.drho = f[row * nxp + x];
-        for (int a = 0; a < 3; ++a) {
-            c.u[a] = f[((a + 1) * nr + row) * nxp + x];
-            c.F[a] = T(0);
-        }
-        // om = 1 and F = 0 make collide_store write exactly g^eq, whose
-        // moments are drho and rho u.
-        T g[Q], jeq[3];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = T(0);
-        for (int a = 0; a < 3; ++a) jeq[a] = (p.rho0 + c.drho) * c.u[a];
-        collide_store<Q, T>(g, c, jeq, p.rho0, T(1), p.out[s], nr * nxp, row * nxp + x);
-        if (R.slot >= 0) {
-            const int ns = p.n_slots[cls];
-            const int off = water ? 0 : 3 * k;
-            for (int a = 0; a < 3; ++a) p.U0[cls][((a + off) * ns + R.slot) * nxp + x] = c.u[a];
-        }
-    }
+    if (!reduced_storage(storage)) return cudaErrorInvalidValue;
+    return Q == 9 ? launch_ref_q9(args, enc, dec, s) : launch_ref_q19(args, enc, dec, s);
 }
 
 // Deterministic final reduction of the per-block partial sums (one block).
@@ -518,155 +48,6 @@ __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ par
         if (threadIdx.x == 0) sums[k] = red[0];
         __syncthreads();
     }
-}
-
-// ---------------------------------------------------------------------------
-// Step kernel.
-//
-// One block per work item (one row, up to 128 consecutive x), one cell per
-// thread, no shared memory and no barriers.  Memory parallelism comes from
-// residency: in FP32 the kernel is held to 64 registers (8 blocks of 128
-// threads per SM), and every thread issues its Q (or 2Q) loads back to back.  The row
-// table is read with 16-byte loads (one 128-byte line per row, cached); the x
-// shift of each direction is a compile-time constant except on the few rows
-// where an x-moving population bounces back.  A solid cell streams, and
-// takes the moments of, both its electrons and phonons, then collides and
-// stores the electrons before pulling the phonons a second time (the lines
-// are still cached), so that at most Q populations are live at once.
-
-// Pull-stream the Q populations of one species at x: p0 = x, pm = x - 1 and
-// pp = x + 1 with periodic wrap.
-template <int Q, typename T>
-__device__ __forceinline__ void pull_row(const T *__restrict__ in, const int src[Q], uint32_t xm,
-                                         uint32_t xp, bool xbounce, int x, int pm, int pp, T g[Q])
-{
-    if (!xbounce) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int xs = cx<Q>(i) > 0 ? pm : (cx<Q>(i) < 0 ? pp : x);
-            g[i] = __ldg(in + src[i] + xs);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int xs = ((xm >> i) & 1u) ? pm : (((xp >> i) & 1u) ? pp : x);
-            g[i] = __ldg(in + src[i] + xs);
-        }
-    }
-}
-
-// The kernel reads the row record as eight 16-byte words.
-static_assert(offsetof(RowInfo, xm) == 19 * 4 && offsetof(RowInfo, xp) == 20 * 4 &&
-                  offsetof(RowInfo, slot) == 21 * 4 && offsetof(RowInfo, flags) == 28 * 4,
-              "row record layout");
-
-template <int Q, typename T>
-__global__ void __launch_bounds__(kBlockX, sizeof(T) == 4 ? 8 : 4) k_step(const StepArgs<T> p)
-{
-    const int b = blockIdx.x;
-    const bool water = b < p.nbw;
-    const int bb = water ? b : b - p.nbw;
-    const int row = bb / p.nchunk;
-    const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
-    const int pm = x == 0 ? p.nx - 1 : x - 1;
-    const int pp = x == p.nx - 1 ? 0 : x + 1;
-    const int nxp = p.nxp;
-
-    const RowInfo &R = p.rows[water ? kFluid : kSolid][row];
-    const int4 *t4 = reinterpret_cast<const int4 *>(&R);
-    int src[20];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-        const int4 q = __ldg(t4 + v);
-        src[4 * v] = q.x;
-        src[4 * v + 1] = q.y;
-        src[4 * v + 2] = q.z;
-        src[4 * v + 3] = q.w;
-    }
-    const uint32_t xm = (uint32_t)src[19];  // the 20th word of a row is its xm mask
-    const int4 q5 = __ldg(t4 + 5);          // xp, slot, nface, partner[0]
-    const int4 q7 = __ldg(t4 + 7);          // flags, pad, pad, pad
-    const uint32_t xp = (uint32_t)q5.x;
-    const bool xbounce = (q7.x & kXBounce) != 0;
-
-    if (water) {
-        T g[Q], j[3];
-        Cell<T> c;
-        pull_row<Q, T>(p.in[0], src, xm, xp, xbounce, x, pm, pp, g);
-        water_math<Q, T>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, x, g, c, j);
-        if (q5.y >= 0) {
-            const int ns = p.n_slots[kFluid];
-            for (int a = 0; a < 3; ++a) p.U0[kFluid][(a * ns + q5.y) * nxp + x] = c.u[a];
-        }
-        collide_store<Q, T>(g, c, j, p.rho0, p.om[0], p.out[0], p.n_rows[kFluid] * nxp, row * nxp + x);
-        return;
-    }
-    T ge[Q], gp[Q], je[3], jp[3];
-    Cell<T> ce, cp;
-    pull_row<Q, T>(p.in[1], src, xm, xp, xbounce, x, pm, pp, ge);
-    pull_row<Q, T>(p.in[2], src, xm, xp, xbounce, x, pm, pp, gp);
-    solid_math<Q, T>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, x, ge, gp, ce,
-                     cp, je, jp);
-    if (q5.y >= 0) {
-        const int ns = p.n_slots[kSolid];
-        for (int a = 0; a < 3; ++a) {
-            p.U0[kSolid][(a * ns + q5.y) * nxp + x] = ce.u[a];
-            p.U0[kSolid][((a + 3) * ns + q5.y) * nxp + x] = cp.u[a];
-        }
-    }
-    const int stride = p.n_rows[kSolid] * nxp, base = row * nxp + x;
-    collide_store<Q, T>(ge, ce, je, p.rho0, p.om[1], p.out[1], stride, base);
-    pull_row<Q, T>(p.in[2], src, xm, xp, xbounce, x, pm, pp, gp);
-    collide_store<Q, T>(gp, cp, jp, p.rho0, p.om[2], p.out[2], stride, base);
-}
-
-// ---------------------------------------------------------------------------
-// Launchers
-
-template <int Q, typename T>
-static cudaError_t launch_plain_step(const StepArgs<T> &a, int nblocks, int bx, cudaStream_t s)
-{
-    k_step<Q, T><<<nblocks, bx, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int Q, typename T>
-static cudaError_t launch_step_t(const void *args, int mode, int nblocks, int bx, cudaStream_t s)
-{
-    const StepArgs<T> &a = *static_cast<const StepArgs<T> *>(args);
-    if (mode == kModeStep) return launch_plain_step<Q, T>(a, nblocks, bx, s);
-    if (mode == kModeObserve)
-        k_lattice<Q, T, kModeObserve><<<nblocks, bx, 0, s>>>(a);
-    else
-        k_lattice<Q, T, kModeField><<<nblocks, bx, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_step(int Q, int storage, const void *args, int mode, int nblocks, int bx,
-                        cudaStream_t s)
-{
-    if (Q == 9)
-        return storage == KLB_FP64 ? launch_step_t<9, double>(args, mode, nblocks, bx, s)
-                                   : launch_step_t<9, float>(args, mode, nblocks, bx, s);
-    return storage == KLB_FP64 ? launch_step_t<19, double>(args, mode, nblocks, bx, s)
-                               : launch_step_t<19, float>(args, mode, nblocks, bx, s);
-}
-
-cudaError_t launch_init(int Q, int storage, const void *args, int nblocks, int bx, cudaStream_t s)
-{
-    if (Q == 9) {
-        if (storage == KLB_FP64)
-            k_init<9, double><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<double> *>(args));
-        else
-            k_init<9, float><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<float> *>(args));
-    } else {
-        if (storage == KLB_FP64)
-            k_init<19, double><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<double> *>(args));
-        else
-            k_init<19, float><<<nblocks, bx, 0, s>>>(*static_cast<const StepArgs<float> *>(args));
-    }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s)

@@ -69,8 +69,12 @@ PIPE_D3Q19_LARGE = PIPE_D3Q19_FP32.with_(
 PIPE_D3Q19_SUB = PIPE_D3Q19_FP32.with_(
     name="d3q19_pipe_128x64x64_r24", nx=128, ny=64, nz=64, radius=24, shell=3)
 
+# The scaled nanotube with populations stored in 16 bits (FP32 arithmetic).
+PIPE_D3Q19_FP16 = PIPE_D3Q19_LARGE.with_(name="d3q19_fp16_pipe_768x192x192_r72", storage="fp16")
+PIPE_D3Q19_BF16 = PIPE_D3Q19_LARGE.with_(name="d3q19_bf16_pipe_768x192x192_r72", storage="bf16")
+
 PRESETS = {w.name: w for w in (SLAB_D2Q9_FP64, PIPE_D3Q19_FP32, PIPE_D3Q19_LARGE,
-                               PIPE_D3Q19_SUB)}
+                               PIPE_D3Q19_SUB, PIPE_D3Q19_FP16, PIPE_D3Q19_BF16)}
 
 
 def perturbation(w: Workload, seed: int, eps: float):

@@ -21,7 +21,8 @@ from . import build as _build
 KLB_D2Q9, KLB_D3Q19 = 9, 19
 KLB_STATIC_MAX_BLOCKS = 49152
 KLB_GEOM_SLAB, KLB_GEOM_PIPE, KLB_GEOM_MASK = 0, 1, 2
-KLB_FP64, KLB_FP32 = 0, 1
+KLB_FP64, KLB_FP32, KLB_FP16_DEV, KLB_BF16_DEV = 0, 1, 2, 3
+STORAGE = {"fp64": KLB_FP64, "fp32": KLB_FP32, "fp16": KLB_FP16_DEV, "bf16": KLB_BF16_DEV}
 KLB_IFACE_SPECULAR, KLB_IFACE_BOUNCEBACK = 0, 1
 STATUS = {0: "KLB_OK", 1: "KLB_EINVAL", 2: "KLB_ENOMEM", 3: "KLB_ECUDA", 4: "KLB_EUNSTABLE",
           5: "KLB_ETIMEOUT", 6: "KLB_ESTATE"}
@@ -269,7 +270,7 @@ def residual_is_valid(obs: dict) -> bool:
 def desc_from_workload(w, nx=None) -> klb_desc:
     """klb_desc of an ``inputs.Workload`` (optionally with another nx)."""
     geom = {"slab": KLB_GEOM_SLAB, "pipe": KLB_GEOM_PIPE, "mask": KLB_GEOM_MASK}[w.geom]
-    storage = {"fp64": KLB_FP64, "fp32": KLB_FP32}[w.storage]
+    storage = STORAGE[w.storage]
     iface = {"specular": KLB_IFACE_SPECULAR, "bounceback": KLB_IFACE_BOUNCEBACK}[w.iface_bc]
     return make_desc(kind=w.kind, nx=nx or w.nx, ny=w.ny, nz=w.nz, geom=geom, width=w.width,
                      radius=w.radius, shell=w.shell, mask=w.extra.get("mask"),

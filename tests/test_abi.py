@@ -89,3 +89,11 @@ def test_mask_geometry_and_empty_species():
                       mask=np.ones((1, 4), np.uint8), periodic_y=True)
     with pytest.raises(klb.KLBError, match="no solid"):
         klb.klb_lattice_info(d)
+
+
+def test_reduced_storage_halves_the_population_footprint():
+    w = inputs.PIPE_D3Q19_FP32
+    b32 = klb.klb_lattice_bytes(klb.desc_from_workload(w))
+    for st in ("fp16", "bf16"):
+        b16 = klb.klb_lattice_bytes(klb.desc_from_workload(w.with_(storage=st)))
+        assert b16 < 0.62 * b32

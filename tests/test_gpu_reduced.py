@@ -1,0 +1,149 @@
+"""GPU parity of reduced-precision storage (FP16 / BF16 differences from a
+per-row FP32 reference, FP32 arithmetic) against the FP64 oracle, and the
+full-size nanotube against the oracle.
+
+Tolerances come from the bound each case must meet (flow rate and slip
+length within 1% for 16-bit storage, slip length within 0.1% for FP32) and,
+for the velocity fields, from the errors measured on GB300 with a margin of
+about 2x (small pipe after 10^4 steps: FP32 1.2e-6, FP16 4.6e-6, BF16 2.5e-5;
+perturbed start after 2000 steps: FP16 4.2e-4, BF16 2.6e-3; full nanotube
+after 5000 steps: FP32 1.7e-5, FP16 1.6e-5, BF16 2.3e-5).
+"""
+import numpy as np
+import pytest
+
+from klb_testutil import make_oracle, rel_l2, species_masks
+from oracle import observables_from_fields
+from paper_2403_15768_gb300 import inputs, klb
+
+pytestmark = pytest.mark.gpu
+
+SMALL_PIPE = inputs.PIPE_D3Q19_FP32.with_(name="pipe_r8", nx=20, ny=24, nz=24, radius=8, shell=3,
+                                          couplings=(0.05, 0.02, 0.1, 0.0, 0.01))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    klb.load_library()
+
+
+def _run_pair(w, storage, seed, steps, oracle_cache={}):
+    key = (repr(w), seed, steps)
+    if key not in oracle_cache:
+        o = make_oracle(w)
+        if seed is not None:
+            d, u = inputs.perturbation(w, seed, 1e-3)
+            o.init_equilibrium(d, u)
+        else:
+            o.init_equilibrium()
+        o.step(steps)
+        f = o.observe()
+        oracle_cache[key] = (o.geo, f, observables_from_fields(o.geo, w.nx, w.rho0, f))
+    geo, f, ob_o = oracle_cache[key]
+    lat = klb.lattice_from_workload(w.with_(storage=storage))
+    if seed is not None:
+        d, u = inputs.perturbation(w, seed, 1e-3)
+        lat.init_equilibrium(d, u)
+    lat.step(steps)
+    _, ug = lat.get_field()
+    m = species_masks(geo, w.nx)
+    errs = [rel_l2(ug[s][:, m[s]], f["u"][s][:, m[s]]) for s in range(3)]
+    return errs, lat.observables(), ob_o
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 1e-5), ("bf16", 6e-5)])
+def test_reduced_quiescent_10k_small_pipe(storage, tol):
+    errs, ob, ob_o = _run_pair(SMALL_PIPE, storage, None, 10_000)
+    assert max(errs) <= tol, errs
+    assert ob["flow_rate"] == pytest.approx(ob_o["flow_rate"], rel=1e-5)
+    assert ob["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 1e-3), ("bf16", 6e-3)])
+def test_reduced_perturbed_start(storage, tol):
+    errs, ob, ob_o = _run_pair(SMALL_PIPE, storage, 1, 2000)
+    assert max(errs) <= tol, errs
+    assert ob["flow_rate"] == pytest.approx(ob_o["flow_rate"], rel=1e-2)
+    assert ob["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-2)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-5), ("bf16", 5e-5)])
+def test_reduced_d2q9_slab_10k(storage, tol):
+    w = inputs.SLAB_D2Q9_FP64.with_(storage="fp32")
+    errs, ob, ob_o = _run_pair(w, storage, None, 10_000)
+    assert max(errs) <= tol, errs
+    assert ob["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
+
+
+_FULL = {}
+
+
+def _full_oracle():
+    """Oracle of the 512x128x128 nanotube from rest, on one x plane: a
+    quiescent start stays exactly x-invariant, so every x plane of the full
+    lattice must equal it."""
+    if not _FULL:
+        w = inputs.PIPE_D3Q19_FP32
+        o = make_oracle(w, nx=1)
+        o.init_equilibrium()
+        o.step(5000)
+        f = o.observe()
+        _FULL["geo"], _FULL["f"] = o.geo, f
+        _FULL["obs"] = observables_from_fields(o.geo, 1, w.rho0, f)
+    return _FULL["geo"], _FULL["f"], _FULL["obs"]
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 3.5e-5), ("fp16", 3.5e-5), ("bf16", 5e-5)])
+def test_full_nanotube_5000_steps_against_oracle(storage, tol):
+    """The 512x128x128 nanotube in the benchmark's launch configuration, 5000
+    steps from rest, against the oracle: slip length within 0.1% (FP32) and
+    flow rate within 1e-4; velocity field within the stated tolerance."""
+    import torch
+
+    geo, f, ob_o = _full_oracle()
+    w = inputs.PIPE_D3Q19_FP32.with_(storage=storage)
+    lat = klb.lattice_from_workload(w)
+    lat.step(5000)
+    _, ug = lat.get_field()
+    ob = lat.observables()
+    m = species_masks(geo, 1)
+    for s in range(3):
+        assert np.abs(ug[s] - ug[s][..., :1]).max() == 0.0  # every x plane identical
+        assert rel_l2(ug[s][..., :1][:, m[s]], f["u"][s][:, m[s]]) <= tol
+    assert ob["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
+    assert ob["flow_rate"] == pytest.approx(ob_o["flow_rate"], rel=1e-4)  # both per unit length
+    del lat
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reduced_state_roundtrip_and_one_step(storage):
+    """klb_set_state encodes against the state's x-averages; reading it back
+    returns each population within the 16-bit precision of its difference
+    from that average; one step from the oracle's state matches the oracle."""
+    w = SMALL_PIPE.with_(nx=40, storage=storage)
+    o = make_oracle(w)
+    d, u = inputs.perturbation(w, 3, 1e-3)
+    o.init_equilibrium(d, u)
+    o.step(20)
+    g, U1, U2 = o.get_state()
+    lat = klb.lattice_from_workload(w)
+    lat.set_state(g, U1, U2, step=20)
+    g_back, _, _ = lat.get_state()
+    # g_back = f32(s16((f32(g) - ref) * 2^k) / 2^k + ref), ref = f32(mean over x):
+    # the 16-bit rounding of the difference plus three FP32 roundings of g.
+    dev = g - g.mean(axis=-1, keepdims=True)
+    rel = 2.0 ** -11 if storage == "fp16" else 2.0 ** -8
+    eps32 = 2.0 ** -24
+    bound = rel * (np.abs(dev) + eps32 * np.abs(g).max()) + 4 * eps32 * np.abs(g) + 1e-13
+    assert np.all(np.abs(g_back - g) <= bound)
+    o.step(1)
+    lat.step(1)
+    _, ug = lat.get_field()
+    f = o.observe()
+    m = species_masks(o.geo, w.nx)
+    for s in range(3):
+        assert rel_l2(ug[s][:, m[s]], f["u"][s][:, m[s]]) <= (1e-3 if storage == "fp16" else 6e-3)
