@@ -42,7 +42,7 @@ def _peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("klb_kernels.cu", "klb_internal.h"):
+    for f in ("klb_kernels.cuh", "klb_internal.h"):
         with open(os.path.join(ROOT, "paper_2403_15768_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -253,6 +253,158 @@ klb_status klb_get_state(klb_lattice *lat, double *g, double *U1, double *U2);
 klb_status klb_set_state(klb_lattice *lat, const double *g, const double *U1,
                          const double *U2, int64_t step);
 
+/*
+ * Batches: many independent lattices stepped together, one kernel launch per
+ * lattice step for all of them (design sweeps over channels of different
+ * sizes and parameters).  All members share the lattice kind, the storage
+ * type and the CUDA stream; they may stand at different time levels (a
+ * request admitted while others run).  A member's step pattern (state buffer
+ * parity, lagged-velocity ring slot and, for 16-bit storage, reference
+ * generation and refresh) repeats after 6 steps, or 384 with 16-bit storage,
+ * so one table of per-lattice kernel arguments per phase of that period
+ * describes every step.  The
+ * tables live in the caller's device buffer (klb_batch_bytes); a whole
+ * period is captured once in a CUDA graph and replayed.  The batch enqueues
+ * its work on a stream of its own, ordered after and before the members'
+ * stream with events.  Members stay usable on their own between batch calls
+ * (observables, fields, state); stepping a member alone takes it out of phase
+ * and the next batch call fails with KLB_ESTATE.
+ */
+typedef struct klb_batch klb_batch;
+
+/* Device bytes a batch of these members needs (0 if they cannot form one). */
+size_t klb_batch_bytes(klb_lattice *const *members, int n);
+
+/* Form a batch in the caller's device buffer (256-byte aligned, at least
+ * klb_batch_bytes).  The members must outlive the batch.  KLB_EINVAL if they
+ * differ in kind, storage or stream, or one appears twice; KLB_ENOMEM if the
+ * buffer is too small. */
+klb_status klb_batch_create(klb_lattice *const *members, int n, void *dev_buf, size_t bytes,
+                            klb_batch **out);
+
+/* Advance every member by nsteps >= 0 steps.  Asynchronous on the members'
+ * stream. */
+klb_status klb_batch_step(klb_batch *b, int64_t nsteps);
+
+/* Time steps_per_candidate >= 1 steps of the batch with each block width
+ * (32, 64 and 128 consecutive x per thread block) and keep the fastest; the
+ * timed steps are real steps of the members.  *width (may be NULL) receives
+ * the chosen width.  Synchronises. */
+klb_status klb_batch_autotune(klb_batch *b, int steps_per_candidate, int *width);
+
+/* Block width in use (128 unless autotuned) and total blocks per step. */
+int klb_batch_width(const klb_batch *b);
+int64_t klb_batch_blocks(const klb_batch *b);
+
+/* Release the batch (not its members or buffer).  Synchronises. */
+klb_status klb_batch_destroy(klb_batch *b);
+
+/* Message of the last failing call on the batch ("" if none). */
+const char *klb_batch_last_error(const klb_batch *b);
+
+/*
+ * Serving: a request loop for design-sweep solves (no counterpart in the
+ * paper, which runs no simulations).  Requests (a lattice description, its
+ * couplings, a residual tolerance and limits) may be submitted at any time.
+ * The server keeps admitted lattices resident in one caller-provided device
+ * arena, admits queued requests first come first served as arena space and
+ * member slots free up (a request waits while the one ahead of it does not
+ * fit), advances every resident lattice together as one batch, and retires
+ * each when its residual (klb_obs.residual) is at most its tolerance, or it
+ * reaches its step or time limit, or turns non-finite.
+ *
+ * klb_server_tick runs one scheduling round: retirement checks of every
+ * resident lattice, admissions, re-forming of the batch when its membership
+ * changed (with an optional block-width autotune whose steps count as part
+ * of the round), then `check_every` steps of the batch.  Every resident
+ * lattice therefore advances by exactly check_every steps per round and is
+ * checked at multiples of check_every steps since its admission, so a
+ * request's result (steps, observables) does not depend on which other
+ * requests shared the GPU with it.  Times are seconds on the server's
+ * monotonic host clock (klb_server_clock).  Not thread-safe.
+ */
+typedef struct klb_server klb_server;
+
+typedef struct {
+    int32_t kind;          /* lattice kind of every request                  */
+    int32_t storage;       /* storage of every request                       */
+    int32_t check_every;   /* steps per round (>= 1)                         */
+    int32_t max_resident;  /* most lattices resident at once (>= 1)          */
+    int32_t autotune_steps;/* > 0: when the batch is re-formed, time 3
+                              candidate block widths over this many steps
+                              each (plus one warm-up) inside the round;
+                              needs check_every >= 3 (autotune_steps + 1)     */
+    int32_t pad;
+} klb_server_opts;
+
+typedef struct {
+    klb_desc desc;         /* MASK cross-sections are copied at submission */
+    klb_couplings couplings;
+    double tol;            /* retire when residual <= tol (> 0)            */
+    int64_t max_steps;     /* step limit (> 0), KLB_ETIMEOUT when reached  */
+    double max_seconds;    /* limit on time since arrival (0: none)        */
+    double arrival;        /* arrival time (server clock); < 0: now        */
+    int64_t id;            /* caller's tag, returned in the result         */
+} klb_request;
+
+typedef struct {
+    int64_t id;
+    int32_t status;        /* KLB_OK converged; KLB_ETIMEOUT step or time
+                              limit; KLB_EUNSTABLE non-finite values; other
+                              codes if creation failed on the device        */
+    int32_t pad;
+    int64_t steps;         /* steps run                                    */
+    int64_t sites;         /* active sites (fluid + solid cells)           */
+    uint64_t bytes;        /* arena bytes held                             */
+    double arrival, admitted, finished;  /* server clock                 */
+    klb_obs obs;           /* observables at retirement                    */
+} klb_result;
+
+typedef struct {
+    int64_t queued, resident, finished;
+    int64_t rounds, batch_forms;
+    uint64_t arena_bytes, bytes_in_use, peak_bytes_in_use, table_bytes;
+    double site_updates;   /* sum over rounds of resident sites x steps      */
+    int32_t width;         /* block width of the current batch (0: none)    */
+    int32_t pad;
+} klb_server_stats;
+
+/* Device bytes reserved in the arena for batch argument tables of up to
+ * max_resident lattices of this storage. */
+size_t klb_server_table_bytes(int storage, int max_resident);
+
+/* Create a server over the caller's device arena (256-byte aligned,
+ * larger than klb_server_table_bytes) on `stream` (NULL: legacy default
+ * stream).  The arena stays owned by the caller and must outlive the
+ * server.  KLB_EINVAL for bad options. */
+klb_status klb_server_create(void *arena, size_t arena_bytes, void *stream,
+                             const klb_server_opts *opts, klb_server **out);
+
+/* Queue a request.  KLB_EINVAL for an invalid description, couplings or
+ * limits, a kind or storage other than the server's, or a lattice that could
+ * never fit in the arena (nothing is queued then). */
+klb_status klb_server_submit(klb_server *srv, const klb_request *req);
+
+/* One scheduling round (see above).  Synchronises.  *n_finished (may be
+ * NULL) receives the number of results now waiting in klb_server_poll. */
+klb_status klb_server_tick(klb_server *srv, int64_t *n_finished);
+
+/* Move up to max finished results, oldest first, into out; returns the
+ * number moved. */
+int64_t klb_server_poll(klb_server *srv, klb_result *out, int64_t max);
+
+/* Counters and the server clock. */
+klb_status klb_server_get_stats(const klb_server *srv, klb_server_stats *st);
+double klb_server_clock(const klb_server *srv);
+
+/* Release the server and every resident lattice (not the arena); queued
+ * requests are dropped.  Synchronises. */
+klb_status klb_server_destroy(klb_server *srv);
+
+/* Message of the last failing call on the server ("" if none); a message
+ * for a failed creation when srv is NULL. */
+const char *klb_server_last_error(const klb_server *srv);
+
 /* Number of completed steps, lattice sizes and species-cell counts. */
 int64_t klb_get_step(const klb_lattice *lat);
 int64_t klb_species_cells(const klb_lattice *lat, int species);

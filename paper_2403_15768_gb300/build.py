@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libklb.so")
 SOURCES = ["klb_kernels_q19.cu", "klb_kernels_q9.cu", "klb_kernels.cu", "klb_geometry.cpp",
-           "klb_api.cpp", "klb_static.cu"]
+           "klb_api.cpp", "klb_static.cu", "klb_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

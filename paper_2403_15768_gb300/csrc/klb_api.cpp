@@ -2,6 +2,7 @@
 // a caller-provided device buffer, couplings, initial state, time stepping,
 // FP64 observables and host access to fields and state.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,6 +19,17 @@
 
 using namespace klb;
 
+// Host view of the time level of a lattice: steps taken, buffer holding the
+// current state, and (reduced-precision storage) the reference generation of
+// each buffer and whether the next step switches to refreshed references.
+struct HostState {
+    int64_t step = 0;
+    int64_t since_reset = 0;  // steps since creation / init / set_state
+    int cur = 0;              // state buffer holding g*(n-1)
+    int gen_buf[2] = {0, 0};
+    bool refresh_pending = false;
+};
+
 struct klb_lattice {
     klb_desc desc;
     std::vector<uint8_t> mask;
@@ -26,13 +38,7 @@ struct klb_lattice {
     cudaStream_t stream = nullptr;
     char *base = nullptr;
     klb_couplings cp{0, 0, 0, 0, 0};
-    int64_t step = 0;
-    int64_t since_reset = 0;  // steps since creation / init / set_state
-    int cur = 0;              // state buffer holding g*(n-1)
-    // Reduced-precision storage: reference generation each state buffer is
-    // encoded with, and whether the next step switches to refreshed references.
-    int gen_buf[2] = {0, 0};
-    bool refresh_pending = false;
+    HostState st;
     std::string err;
 };
 
@@ -69,23 +75,25 @@ void *dev(const klb_lattice *L, size_t off) { return L->base + off; }
 // Lagged-velocity slot of step m (slots rotate with period 3).
 int slot_of(int64_t m) { return (int)(((m % 3) + 3) % 3); }
 
+// Kernel arguments for the time level `st` (the step about to run, or the
+// one observed) with blocks of bx consecutive x.
 template <typename T>
-void fill_args(const klb_lattice *L, StepArgs<T> &a)
+void fill_args_at(const klb_lattice *L, const HostState &st, int bx, StepArgs<T> &a)
 {
     const Geometry &g = L->geo;
     const MemoryPlan &p = L->plan;
     std::memset(&a, 0, sizeof a);
-    const int n = (int)L->step;  // the step about to run / being observed
+    const int64_t n = st.step;
     for (int s = 0; s < 3; ++s) {
-        a.in[s] = dev(L, p.pop[L->cur][s]);
-        a.out[s] = dev(L, p.pop[1 - L->cur][s]);
-        a.in_prev[s] = dev(L, p.pop[1 - L->cur][s]);
+        a.in[s] = dev(L, p.pop[st.cur][s]);
+        a.out[s] = dev(L, p.pop[1 - st.cur][s]);
+        a.in_prev[s] = dev(L, p.pop[1 - st.cur][s]);
     }
     if (reduced(L)) {
         for (int s = 0; s < 3; ++s) {
-            a.dec_in[s] = (const float *)dev(L, p.ref_dec[L->gen_buf[L->cur]][s]);
-            a.dec_prev[s] = (const float *)dev(L, p.ref_dec[L->gen_buf[1 - L->cur]][s]);
-            a.enc_out[s] = (const float *)dev(L, p.ref_enc[L->gen_buf[L->cur]][s]);
+            a.dec_in[s] = (const float *)dev(L, p.ref_dec[st.gen_buf[st.cur]][s]);
+            a.dec_prev[s] = (const float *)dev(L, p.ref_dec[st.gen_buf[1 - st.cur]][s]);
+            a.enc_out[s] = (const float *)dev(L, p.ref_enc[st.gen_buf[st.cur]][s]);
         }
         a.scale = L->desc.storage == KLB_FP16_DEV ? kFp16Scale : 1.0f;
         a.inv_scale = 1.0f / a.scale;
@@ -104,8 +112,10 @@ void fill_args(const klb_lattice *L, StepArgs<T> &a)
     }
     a.nx = g.nx;
     a.nxp = g.nxp;
-    a.nchunk = p.nchunk;
-    a.nbw = p.nblocks_w;
+    a.nchunk = (g.nx + bx - 1) / bx;
+    a.nbw = (int)g.rows[kFluid].size() * a.nchunk;
+    a.nch32 = (g.nx + 31) / 32;
+    a.nseg_w = (int)g.rows[kFluid].size() * a.nch32;
     const klb_desc &d = L->desc;
     a.rho0 = (T)d.rho0;
     a.om[0] = (T)(1.0 / d.tau_w);
@@ -118,8 +128,42 @@ void fill_args(const klb_lattice *L, StepArgs<T> &a)
     a.g_ec = (T)L->cp.g_ec;
     a.g_pc = (T)L->cp.g_pc;
     a.partials = (double *)dev(L, p.partials);
-    a.residual_valid = L->since_reset >= 2;
+    a.residual_valid = st.since_reset >= 2;
     a.field = (T *)dev(L, p.field);
+}
+
+template <typename T>
+void fill_args(const klb_lattice *L, StepArgs<T> &a)
+{
+    fill_args_at(L, L->st, L->plan.bx, a);
+}
+
+// The host side of one step: encode generation of the output, whether the
+// step accumulates x-sums for a reference refresh, and whether a refresh
+// into that generation must run before it.
+struct StepPlan {
+    int outgen;
+    bool acc;
+    bool refresh;
+};
+
+StepPlan plan_step(const HostState &st, bool red)
+{
+    StepPlan sp;
+    sp.outgen = st.gen_buf[st.cur];
+    sp.refresh = red && st.refresh_pending;
+    if (sp.refresh) sp.outgen = 1 - st.gen_buf[st.cur];
+    sp.acc = red && (st.step + 1) % kRefEvery == 0;
+    return sp;
+}
+
+void advance(HostState &st, const StepPlan &sp)
+{
+    st.gen_buf[1 - st.cur] = sp.outgen;
+    st.cur = 1 - st.cur;
+    ++st.step;
+    ++st.since_reset;
+    st.refresh_pending = sp.acc;
 }
 
 // Runs `body(args)` with arguments of the lattice's arithmetic type.
@@ -204,11 +248,11 @@ klb_status init_from_fields(klb_lattice *L, const double *drho, const double *u)
     host_to_field<T>(L, drho, u, f);
     KLB_CUDA(L, cudaMemcpyAsync(dev(L, L->plan.field), f.data(), L->plan.field_bytes,
                                 cudaMemcpyHostToDevice, L->stream));
-    L->cur = 0;
-    L->step = 0;
-    L->since_reset = 0;
-    L->gen_buf[0] = L->gen_buf[1] = 0;
-    L->refresh_pending = false;
+    L->st.cur = 0;
+    L->st.step = 0;
+    L->st.since_reset = 0;
+    L->st.gen_buf[0] = L->st.gen_buf[1] = 0;
+    L->st.refresh_pending = false;
     const int slot0 = slot_of(0);
     auto init_pass = [&](int mode) {
         return with_args(L, [&](void *a) {
@@ -243,7 +287,7 @@ klb_status finish_observables(klb_lattice *L, const double *S, klb_obs *out)
     const Geometry &g = L->geo;
     const double nan = std::numeric_limits<double>::quiet_NaN();
     std::memset(out, 0, sizeof *out);
-    out->step = L->step;
+    out->step = L->st.step;
     out->flow_rate = S[kSumUxFluid] / g.nx;
     out->d_wall = g.has_fit ? g.d_wall : nan;
     const double n = S[kSumFitN], s2 = S[kSumFitD2], s4 = S[kSumFitD4];
@@ -269,7 +313,7 @@ klb_status finish_observables(klb_lattice *L, const double *S, klb_obs *out)
         out->momentum[s] = S[kSumMomW + s];
         out->mass[s] = S[kSumMassW + s];
     }
-    out->residual = L->since_reset >= 2 ? S[kSumResidual] : nan;
+    out->residual = L->st.since_reset >= 2 ? S[kSumResidual] : nan;
     out->nonfinite = (int64_t)S[kSumNonfinite];
     if (out->nonfinite > 0) return fail(L, KLB_EUNSTABLE, "non-finite density or velocity");
     return KLB_OK;
@@ -396,27 +440,20 @@ klb_status klb_step(klb_lattice *L, int64_t nsteps)
     if (!L) return fail(L, KLB_EINVAL, "null handle");
     if (nsteps < 0) return fail(L, KLB_EINVAL, "nsteps must be >= 0");
     for (int64_t n = 0; n < nsteps; ++n) {
-        int outgen = L->gen_buf[L->cur];
-        if (reduced(L) && L->refresh_pending) {
+        const StepPlan sp = plan_step(L->st, reduced(L));
+        if (sp.refresh) {
             // Decode this step with the current references, encode its output
             // with references refreshed from the last step's x-averages.
-            outgen = 1 - L->gen_buf[L->cur];
-            cudaError_t e = refresh_refs(L, outgen);
+            cudaError_t e = refresh_refs(L, sp.outgen);
             if (e != cudaSuccess) return cuda_fail(L, e, "reference refresh");
-            L->refresh_pending = false;
         }
-        const bool acc = reduced(L) && (L->step + 1) % kRefEvery == 0;
         cudaError_t e = with_args(L, [&](void *a) {
-            set_enc(L, a, outgen);
-            return launch(L->geo.Q, L->desc.storage, a, acc ? kModeStepAcc : kModeStep, nblocks(L),
-                          L->plan.bx, L->stream);
+            set_enc(L, a, sp.outgen);
+            return launch(L->geo.Q, L->desc.storage, a, sp.acc ? kModeStepAcc : kModeStep,
+                          nblocks(L), L->plan.bx, L->stream);
         });
         if (e != cudaSuccess) return cuda_fail(L, e, "step kernel launch");
-        L->gen_buf[1 - L->cur] = outgen;
-        L->cur = 1 - L->cur;
-        ++L->step;
-        ++L->since_reset;
-        if (acc) L->refresh_pending = true;
+        advance(L->st, sp);
     }
     return KLB_OK;
 }
@@ -439,7 +476,7 @@ klb_status klb_observables(klb_lattice *L, klb_obs *out)
     const Geometry &g = L->geo;
     const double nan = std::numeric_limits<double>::quiet_NaN();
     std::memset(out, 0, sizeof *out);
-    out->step = L->step;
+    out->step = L->st.step;
     out->flow_rate = S[kSumUxFluid] / g.nx;
     out->d_wall = g.has_fit ? g.d_wall : nan;
     // Least squares u = A + B d^2 from its normal equations.
@@ -466,7 +503,7 @@ klb_status klb_observables(klb_lattice *L, klb_obs *out)
         out->momentum[s] = S[kSumMomW + s];
         out->mass[s] = S[kSumMassW + s];
     }
-    out->residual = L->since_reset >= 2 ? S[kSumResidual] : nan;
+    out->residual = L->st.since_reset >= 2 ? S[kSumResidual] : nan;
     out->nonfinite = (int64_t)S[kSumNonfinite];
     if (out->nonfinite > 0) return fail(L, KLB_EUNSTABLE, "non-finite density or velocity");
     return KLB_OK;
@@ -564,12 +601,12 @@ klb_status klb_get_state(klb_lattice *L, double *gout, double *U1, double *U2)
         std::memset(gout, 0, sizeof(double) * 3 * Q * ncell);
         for (int s = 0; s < 3; ++s) {
             std::vector<char> raw(L->plan.pop_bytes[s]);
-            KLB_CUDA(L, cudaMemcpyAsync(raw.data(), dev(L, L->plan.pop[L->cur][s]), raw.size(),
+            KLB_CUDA(L, cudaMemcpyAsync(raw.data(), dev(L, L->plan.pop[L->st.cur][s]), raw.size(),
                                         cudaMemcpyDeviceToHost, L->stream));
             std::vector<float> ref;
             if (red) {
                 ref.resize(L->plan.ref_bytes[s] / sizeof(float));
-                KLB_CUDA(L, cudaMemcpyAsync(ref.data(), dev(L, L->plan.ref_enc[L->gen_buf[L->cur]][s]),
+                KLB_CUDA(L, cudaMemcpyAsync(ref.data(), dev(L, L->plan.ref_enc[L->st.gen_buf[L->st.cur]][s]),
                                             L->plan.ref_bytes[s], cudaMemcpyDeviceToHost, L->stream));
             }
             klb_status st = sync(L);
@@ -591,7 +628,7 @@ klb_status klb_get_state(klb_lattice *L, double *gout, double *U1, double *U2)
     for (int t = 0; t < 2; ++t) {
         if (!Uo[t]) continue;
         std::memset(Uo[t], 0, sizeof(double) * 9 * ncell);
-        const int slot = slot_of(L->step - 1 - t);
+        const int slot = slot_of(L->st.step - 1 - t);
         for (int c = 0; c < 2; ++c) {
             const size_t ns = g.slot_row[c].size();
             if (!ns) continue;
@@ -653,11 +690,11 @@ klb_status klb_set_state(klb_lattice *L, const double *gin, const double *U1, co
             ((float *)raw.data())[k] = (float)v;
     };
     KLB_CUDA(L, cudaStreamSynchronize(L->stream));
-    L->cur = 0;
-    L->step = step;
-    L->since_reset = 0;
-    L->gen_buf[0] = L->gen_buf[1] = 0;
-    L->refresh_pending = false;
+    L->st.cur = 0;
+    L->st.step = step;
+    L->st.since_reset = 0;
+    L->st.gen_buf[0] = L->st.gen_buf[1] = 0;
+    L->st.refresh_pending = false;
     std::vector<float> enc[3];
     for (int s = 0; s < 3; ++s) {
         const int c = cls_of(s);
@@ -731,7 +768,7 @@ klb_status klb_set_state(klb_lattice *L, const double *gin, const double *U1, co
     return KLB_OK;
 }
 
-int64_t klb_get_step(const klb_lattice *L) { return L ? L->step : -1; }
+int64_t klb_get_step(const klb_lattice *L) { return L ? L->st.step : -1; }
 
 int64_t klb_species_cells(const klb_lattice *L, int species)
 {
@@ -755,5 +792,359 @@ const char *klb_last_error(const klb_lattice *L)
 {
     return L ? L->err.c_str() : g_create_error.c_str();
 }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches
+
+struct klb_batch {
+    std::vector<klb_lattice *> mem;
+    cudaStream_t user = nullptr;  // the members' stream
+    cudaStream_t stream = nullptr;  // the batch's own stream (graph capture)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    char *base = nullptr;
+    size_t bytes = 0;
+    int Q = 19, storage = KLB_FP32;
+    int period = 6;
+    int width = kBlockX;
+    int nblocks = 0;
+    size_t args_size = 0, table_off = 0, prefix_off = 0;
+    std::vector<StepPlan> plans;  // per (phase, member)
+    std::vector<char> acc;        // per phase: some member accumulates x-sums
+    std::vector<int64_t> base_step;  // members' steps at phase 0
+    std::vector<HostState> base_state;  // members' time levels at phase 0
+    int64_t phase = 0;               // steps taken since phase 0
+    cudaGraphExec_t graph = nullptr;
+    std::string err;
+};
+
+namespace {
+
+klb_status bfail(klb_batch *B, klb_status st, const std::string &msg)
+{
+    B->err = msg;
+    return st;
+}
+
+#define KLB_BCUDA(B, call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return bfail((B), KLB_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+int batch_period(int storage) { return reduced_storage(storage) ? 6 * 2 * kRefEvery : 6; }
+
+size_t args_size(int storage) { return storage == KLB_FP64 ? sizeof(StepArgs<double>) : sizeof(StepArgs<float>); }
+
+size_t batch_layout(int n, int storage, size_t *table_off, size_t *prefix_off)
+{
+    const size_t tb = (size_t)batch_period(storage) * n * args_size(storage);
+    *table_off = 0;
+    *prefix_off = (tb + 255) / 256 * 256;
+    return *prefix_off + ((size_t)(n + 1) * sizeof(int) + 255) / 256 * 256;
+}
+
+void destroy_graph(klb_batch *B)
+{
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    B->graph = nullptr;
+}
+
+// Per-phase argument tables for block width `width`, from each member's own
+// time level now (phase 0), the block prefix, and the phase plans.  Every
+// member's step pattern repeats after the batch period whatever its step
+// count, so members may stand at different time levels.  A launch
+// accumulates reference x-sums when any member needs them; the x-sums are
+// stored, not added, so an extra pass leaves the other members' refreshes
+// unchanged.
+klb_status build_tables(klb_batch *B, int width)
+{
+    const int n = (int)B->mem.size(), P = B->period;
+    std::vector<char> host((size_t)P * n * B->args_size);
+    std::vector<int> prefix(n + 1, 0);
+    B->plans.assign((size_t)P * n, StepPlan{0, false, false});
+    B->acc.assign(P, 0);
+    for (int m = 0; m < n; ++m) {
+        const klb_lattice *L = B->mem[m];
+        HostState st = L->st;
+        for (int k = 0; k < P; ++k) {
+            const StepPlan sp = plan_step(st, reduced(L));
+            B->plans[(size_t)k * n + m] = sp;
+            B->acc[k] |= (char)sp.acc;
+            char *slot = host.data() + ((size_t)k * n + m) * B->args_size;
+            if (B->storage == KLB_FP64) {
+                StepArgs<double> a;
+                fill_args_at(L, st, width, a);
+                std::memcpy(slot, &a, sizeof a);
+            } else {
+                StepArgs<float> a;
+                fill_args_at(L, st, width, a);
+                if (reduced(L))
+                    for (int s = 0; s < 3; ++s) a.enc_out[s] = (const float *)dev(L, L->plan.ref_enc[sp.outgen][s]);
+                std::memcpy(slot, &a, sizeof a);
+            }
+            advance(st, sp);
+        }
+        const int chunks = (L->geo.nx + width - 1) / width;
+        prefix[m + 1] = prefix[m] + chunks * (int)(L->geo.rows[kFluid].size() + L->geo.rows[kSolid].size());
+    }
+    KLB_BCUDA(B, cudaStreamSynchronize(B->stream));
+    KLB_BCUDA(B, cudaMemcpy(B->base + B->table_off, host.data(), host.size(), cudaMemcpyHostToDevice));
+    KLB_BCUDA(B, cudaMemcpy(B->base + B->prefix_off, prefix.data(), prefix.size() * sizeof(int),
+                            cudaMemcpyHostToDevice));
+    B->width = width;
+    B->nblocks = prefix[n];
+    B->phase = 0;
+    B->base_step.resize(n);
+    B->base_state.resize(n);
+    for (int m = 0; m < n; ++m) {
+        B->base_step[m] = B->mem[m]->st.step;
+        B->base_state[m] = B->mem[m]->st;
+    }
+    destroy_graph(B);
+    return KLB_OK;
+}
+
+// One phase of the batch on its stream: reference refreshes due before the
+// step, then the batched step kernel.
+cudaError_t launch_phase(klb_batch *B, int k)
+{
+    const size_t n = B->mem.size();
+    for (size_t m = 0; m < n; ++m) {
+        const StepPlan &sp = B->plans[k * n + m];
+        if (!sp.refresh) continue;
+        klb_lattice *L = B->mem[m];
+        cudaStream_t keep = L->stream;
+        L->stream = B->stream;
+        cudaError_t e = refresh_refs(L, sp.outgen);
+        L->stream = keep;
+        if (e != cudaSuccess) return e;
+    }
+    const char *table = B->base + B->table_off + (size_t)k * n * B->args_size;
+    return launch_batch(B->Q, B->storage, table, (const int *)(B->base + B->prefix_off), (int)n,
+                        B->nblocks, B->width, B->acc[k] != 0, B->stream);
+}
+
+klb_status capture_graph(klb_batch *B)
+{
+    destroy_graph(B);
+    cudaGraph_t g = nullptr;
+    KLB_BCUDA(B, cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < B->period && e == cudaSuccess; ++k) e = launch_phase(B, k);
+    cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(B, KLB_ECUDA, std::string("graph capture: ") +
+                                       cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&B->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        B->graph = nullptr;
+        return bfail(B, KLB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return KLB_OK;
+}
+
+bool in_phase(const klb_batch *B)
+{
+    for (size_t m = 0; m < B->mem.size(); ++m)
+        if (B->mem[m]->st.step != B->base_step[m] + B->phase) return false;
+    return true;
+}
+
+// Whether every member stands where the tables' phase 0 assumed.  The step
+// pattern repeats after a period from any time level but one: right after
+// an initialisation of 16-bit storage no reference refresh is pending at a
+// multiple of the refresh interval, where one is pending in every later
+// period.
+bool tables_repeat(const klb_batch *B)
+{
+    for (size_t m = 0; m < B->mem.size(); ++m) {
+        const HostState &a = B->mem[m]->st, &b = B->base_state[m];
+        if (a.cur != b.cur || a.gen_buf[0] != b.gen_buf[0] || a.gen_buf[1] != b.gen_buf[1] ||
+            a.refresh_pending != b.refresh_pending)
+            return false;
+    }
+    return true;
+}
+
+// Runs nsteps phases on the batch stream, replaying the graph for whole
+// periods; advances every member's host state.  At the start of each later
+// period the tables are checked against the members' time levels and built
+// again if they no longer describe it.
+klb_status run_steps(klb_batch *B, int64_t nsteps, bool use_graph)
+{
+    while (nsteps > 0) {
+        if (B->phase > 0 && B->phase % B->period == 0 && !tables_repeat(B)) {
+            klb_status st = build_tables(B, B->width);
+            if (st != KLB_OK) return st;
+        }
+        const int k = (int)(B->phase % B->period);
+        if (use_graph && k == 0 && nsteps >= B->period) {
+            if (!B->graph) {
+                klb_status st = capture_graph(B);
+                if (st != KLB_OK) return st;
+            }
+            KLB_BCUDA(B, cudaGraphLaunch(B->graph, B->stream));
+            for (klb_lattice *L : B->mem) {
+                HostState &h = L->st;
+                for (int j = 0; j < B->period; ++j) advance(h, plan_step(h, reduced(L)));
+            }
+            B->phase += B->period;
+            nsteps -= B->period;
+            continue;
+        }
+        KLB_BCUDA(B, launch_phase(B, k));
+        for (klb_lattice *L : B->mem) advance(L->st, plan_step(L->st, reduced(L)));
+        ++B->phase;
+        --nsteps;
+    }
+    return KLB_OK;
+}
+
+}  // namespace
+
+size_t klb::batch_table_bytes(int storage, int n)
+{
+    size_t t, p;
+    return n < 1 ? 0 : batch_layout(n, storage, &t, &p);
+}
+
+extern "C" {
+
+size_t klb_batch_bytes(klb_lattice *const *members, int n)
+{
+    if (!members || n < 1 || !members[0]) return 0;
+    size_t t, p;
+    return batch_layout(n, members[0]->desc.storage, &t, &p);
+}
+
+klb_status klb_batch_create(klb_lattice *const *members, int n, void *dev_buf, size_t bytes,
+                            klb_batch **out)
+{
+    if (!out) return fail(nullptr, KLB_EINVAL, "null argument");
+    *out = nullptr;
+    if (!members || n < 1) return fail(nullptr, KLB_EINVAL, "a batch needs at least one member");
+    for (int m = 0; m < n; ++m) {
+        const klb_lattice *L = members[m];
+        if (!L) return fail(nullptr, KLB_EINVAL, "null member");
+        if (L->geo.Q != members[0]->geo.Q || L->desc.storage != members[0]->desc.storage)
+            return fail(nullptr, KLB_EINVAL, "batch members must share lattice kind and storage");
+        if (L->stream != members[0]->stream)
+            return fail(nullptr, KLB_EINVAL, "batch members must share one CUDA stream");
+        for (int k = 0; k < m; ++k)
+            if (members[k] == L) return fail(nullptr, KLB_EINVAL, "a lattice appears twice in the batch");
+    }
+    klb_batch *B = new (std::nothrow) klb_batch();
+    if (!B) return fail(nullptr, KLB_ENOMEM, "host allocation failed");
+    B->mem.assign(members, members + n);
+    B->Q = members[0]->geo.Q;
+    B->storage = members[0]->desc.storage;
+    B->period = batch_period(B->storage);
+    B->args_size = args_size(B->storage);
+    const size_t need = batch_layout(n, B->storage, &B->table_off, &B->prefix_off);
+    if (!dev_buf || ((uintptr_t)dev_buf & 255u)) {
+        delete B;
+        return fail(nullptr, KLB_EINVAL, "dev_buf must be a 256-byte aligned device pointer");
+    }
+    if (bytes < need) {
+        delete B;
+        return fail(nullptr, KLB_ENOMEM, "device buffer smaller than klb_batch_bytes()");
+    }
+    B->base = (char *)dev_buf;
+    B->bytes = bytes;
+    B->user = members[0]->stream;
+    cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->user);
+    if (e != cudaSuccess) {
+        std::string m = std::string("batch setup: ") + cudaGetErrorString(e);
+        klb_batch_destroy(B);
+        return fail(nullptr, KLB_ECUDA, m);
+    }
+    int w = kBlockX;
+    for (klb_lattice *L : B->mem) w = std::min(w, L->plan.bx);
+    klb_status st = build_tables(B, w);
+    if (st != KLB_OK) {
+        std::string m = B->err;
+        klb_batch_destroy(B);
+        return fail(nullptr, st, m);
+    }
+    *out = B;
+    return KLB_OK;
+}
+
+klb_status klb_batch_step(klb_batch *B, int64_t nsteps)
+{
+    if (!B) return KLB_EINVAL;
+    if (nsteps < 0) return bfail(B, KLB_EINVAL, "nsteps must be >= 0");
+    if (!in_phase(B))
+        return bfail(B, KLB_ESTATE, "a member was stepped outside the batch; form the batch again");
+    KLB_BCUDA(B, cudaEventRecord(B->ev_in, B->user));
+    KLB_BCUDA(B, cudaStreamWaitEvent(B->stream, B->ev_in, 0));
+    klb_status st = run_steps(B, nsteps, true);
+    KLB_BCUDA(B, cudaEventRecord(B->ev_out, B->stream));
+    KLB_BCUDA(B, cudaStreamWaitEvent(B->user, B->ev_out, 0));
+    return st;
+}
+
+klb_status klb_batch_autotune(klb_batch *B, int steps_per_candidate, int *width)
+{
+    if (!B) return KLB_EINVAL;
+    if (steps_per_candidate < 1) return bfail(B, KLB_EINVAL, "steps_per_candidate must be >= 1");
+    if (!in_phase(B))
+        return bfail(B, KLB_ESTATE, "a member was stepped outside the batch; form the batch again");
+    KLB_BCUDA(B, cudaStreamSynchronize(B->user));
+    cudaEvent_t t0, t1;
+    KLB_BCUDA(B, cudaEventCreate(&t0));
+    KLB_BCUDA(B, cudaEventCreate(&t1));
+    const int cand[3] = {32, 64, 128};
+    int best = B->width;
+    float best_ms = 1e30f;
+    klb_status st = KLB_OK;
+    for (int c = 0; c < 3 && st == KLB_OK; ++c) {
+        st = build_tables(B, cand[c]);
+        if (st != KLB_OK) break;
+        st = run_steps(B, 1, false);  // warm-up
+        if (st != KLB_OK) break;
+        cudaEventRecord(t0, B->stream);
+        st = run_steps(B, steps_per_candidate, false);
+        cudaEventRecord(t1, B->stream);
+        if (cudaEventSynchronize(t1) != cudaSuccess) st = bfail(B, KLB_ECUDA, "autotune timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (st == KLB_OK && ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (st != KLB_OK) return st;
+    st = build_tables(B, best);
+    if (width) *width = best;
+    return st;
+}
+
+int klb_batch_width(const klb_batch *B) { return B ? B->width : 0; }
+int64_t klb_batch_blocks(const klb_batch *B) { return B ? B->nblocks : 0; }
+
+klb_status klb_batch_destroy(klb_batch *B)
+{
+    if (!B) return KLB_OK;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    destroy_graph(B);
+    if (B->ev_in) cudaEventDestroy(B->ev_in);
+    if (B->ev_out) cudaEventDestroy(B->ev_out);
+    if (B->stream) cudaStreamDestroy(B->stream);
+    delete B;
+    return KLB_OK;
+}
+
+const char *klb_batch_last_error(const klb_batch *B) { return B ? B->err.c_str() : ""; }
 
 }  // extern "C"

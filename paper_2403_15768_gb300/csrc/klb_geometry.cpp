@@ -328,7 +328,8 @@ MemoryPlan plan_memory(const Geometry &g, int storage)
                 p.ref_enc[gen][s] = take(p.ref_bytes[s]);
                 p.ref_dec[gen][s] = take(p.ref_bytes[s]);
             }
-        p.acc_bytes = sizeof(float) * 2 * g.Q * (size_t)(p.nblocks_w + p.nblocks_s);
+        const size_t nseg = (nr[kFluid] + nr[kSolid]) * (size_t)((g.nx + 31) / 32);
+        p.acc_bytes = sizeof(float) * 2 * g.Q * nseg;
         p.acc = take(p.acc_bytes);
     }
     p.total = off;

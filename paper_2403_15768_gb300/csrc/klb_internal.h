@@ -112,14 +112,15 @@ inline size_t storage_bytes(int storage)
 // Kernel arguments.  T is the arithmetic type (float or double); the
 // populations are stored as T, or as FP16/BF16 against per-row references.
 template <typename T>
-struct StepArgs {
+struct alignas(16) StepArgs {
     const void *in[3];     // current state, per species
     void *out[3];          // next state (step and init modes)
     const void *in_prev[3];  // previous state (observe mode, residual)
     const RowInfo *rows[2];
     const T *U1[2], *U2[2], *U3[2];  // lagged velocities u(n-1), u(n-2), u(n-3)
     T *U0[2];                        // u(n) written here (step mode)
-    int nx, nxp, nchunk, nbw;
+    int nx, nxp, nchunk, nbw;        // nchunk = x chunks of blockDim.x per row; nbw = water blocks
+    int nch32, nseg_w;               // 32-wide x segments per row; water segments
     int n_rows[2], n_slots[2];
     T rho0, om[3], G[3];
     T g_we, g_wp, g_ep, g_ec, g_pc;
@@ -130,7 +131,7 @@ struct StepArgs {
     const float *dec_in[3], *dec_prev[3];  // references of pulled populations
     const float *enc_out[3];               // references of stored populations
     float scale, inv_scale;
-    float *acc;            // per-block x-sums of g* [block][2Q]
+    float *acc;            // x-sums of g* per 32-wide segment [segment][2Q]
 };
 
 enum Mode {
@@ -149,6 +150,14 @@ cudaError_t launch(int Q, int storage, const void *args, int mode, int nblocks, 
 cudaError_t launch_ref(int Q, int storage, const void *args, float *const enc[3],
                        float *const dec[3], cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s);
+// One step of many lattices in one launch: table[l] holds the arguments of
+// lattice l, prefix[l] its first block (prefix[n] = total blocks).
+cudaError_t launch_batch(int Q, int storage, const void *table, const int *prefix, int n,
+                         int nblocks, int bx, bool acc, cudaStream_t s);
+
+// Device bytes of the argument tables of a batch of n lattices with this
+// storage (the layout klb_batch_create uses).
+size_t batch_table_bytes(int storage, int n);
 
 // Static scratch of klb_observables_static (klb_static.cu): device addresses
 // of its partial-sum rows and final sums on the current device.

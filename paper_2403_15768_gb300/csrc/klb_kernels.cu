@@ -11,6 +11,18 @@ cudaError_t launch_q19(int storage, const void *args, int mode, int nblocks, int
 cudaError_t launch_ref_q9(const void *args, float *const enc[3], float *const dec[3], cudaStream_t s);
 cudaError_t launch_ref_q19(const void *args, float *const enc[3], float *const dec[3], cudaStream_t s);
 
+cudaError_t launch_batch_q9(int storage, const void *table, const int *prefix, int n, int nblocks,
+                          int bx, bool acc, cudaStream_t s);
+cudaError_t launch_batch_q19(int storage, const void *table, const int *prefix, int n, int nblocks,
+                           int bx, bool acc, cudaStream_t s);
+
+cudaError_t launch_batch(int Q, int storage, const void *table, const int *prefix, int n,
+                         int nblocks, int bx, bool acc, cudaStream_t s)
+{
+    return Q == 9 ? launch_batch_q9(storage, table, prefix, n, nblocks, bx, acc, s)
+                  : launch_batch_q19(storage, table, prefix, n, nblocks, bx, acc, s);
+}
+
 cudaError_t launch(int Q, int storage, const void *args, int mode, int nblocks, int bx,
                    cudaStream_t s)
 {

@@ -402,26 +402,27 @@ __device__ inline void block_reduce_store(double (&s)[kNumSums], double *out)
     }
 }
 
-// Per-block x-sums of NV values per thread (post-collision populations of one
-// or two species), written to out[0 .. NV): the partial sums that reference
-// refreshes reduce.  Threads past the end of the row contribute zeros.
+// x-sums over one warp (a 32-wide x segment of a row) of NV values per
+// thread, written by lane 0 to out[0 .. NV): the partial sums that reference
+// refreshes reduce.  Lanes past the end of the row contribute zeros.
 template <int NV>
-__device__ __forceinline__ void block_xsum(const float (&v)[NV], float *out)
+__device__ __forceinline__ void warp_xsum(const float (&v)[NV], float *out)
 {
-    __shared__ float red[NV][kBlockX / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
         const float s = warp_sumf(v[k]);
-        if (lane == 0) red[k][warp] = s;
+        if ((threadIdx.x & 31) == 0) out[k] = s;
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < NV; k += blockDim.x) {
-        float s = red[k][0];
-        for (int w = 1; w < nwarps; ++w) s += red[k][w];
-        out[k] = s;
-    }
+}
+
+// Segment (32-wide x run of a row) of the calling warp, or -1 when the warp
+// lies past the end of its row.
+template <typename T>
+__device__ __forceinline__ int warp_segment(const StepArgs<T> &p, bool water, int row, int x_lane0)
+{
+    const int xw = x_lane0 - (threadIdx.x & 31);
+    if (xw >= p.nx) return -1;
+    return (water ? 0 : p.nseg_w) + row * p.nch32 + xw / 32;
 }
 
 template <typename T>
@@ -594,7 +595,10 @@ __global__ void __launch_bounds__(kBlockX) k_init(const StepArgs<T> p)
             }
         }
     }
-    if constexpr (ACC) block_xsum<2 * Q>(sums, p.acc + (size_t)b * 2 * Q);
+    if constexpr (ACC) {
+        const int seg = warp_segment(p, water, row, x);
+        if (seg >= 0) warp_xsum<2 * Q>(sums, p.acc + (size_t)seg * 2 * Q);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -655,18 +659,18 @@ constexpr int step_min_blocks()
 }
 
 template <int Q, typename T, typename S, bool ACC>
-__global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(const StepArgs<T> p)
+__device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
 {
-    const int b = blockIdx.x;
     const bool water = b < p.nbw;
     const int bb = water ? b : b - p.nbw;
     const int row = bb / p.nchunk;
     int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
+    const int x_lane = x;
     const bool live = x < p.nx;
     if constexpr (!ACC) {
-        if (!live) return;  // no barrier follows
+        if (!live) return;  // no warp-wide operation follows
     } else {
-        if (!live) x = 0;   // computes nothing, but joins the block reduction
+        if (!live) x = 0;   // computes nothing, but joins the warp reduction
     }
     const int pm = x == 0 ? p.nx - 1 : x - 1;
     const int pp = x == p.nx - 1 ? 0 : x + 1;
@@ -712,7 +716,8 @@ __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(con
                 acc[i] = live ? float(g[i]) : 0.f;
                 acc[Q + i] = 0.f;
             }
-            block_xsum<2 * Q>(acc, p.acc + (size_t)b * 2 * Q);
+            const int seg = warp_segment(p, true, row, x_lane);
+            if (seg >= 0) warp_xsum<2 * Q>(acc, p.acc + (size_t)seg * 2 * Q);
         }
         return;
     }
@@ -755,7 +760,46 @@ __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(con
 #pragma unroll
         for (int k = 0; k < 2 * Q; ++k) acc[k] = 0.f;
     }
-    if constexpr (ACC) block_xsum<2 * Q>(acc, p.acc + (size_t)b * 2 * Q);
+    if constexpr (ACC) {
+        const int seg = warp_segment(p, false, row, x_lane);
+        if (seg >= 0) warp_xsum<2 * Q>(acc, p.acc + (size_t)seg * 2 * Q);
+    }
+}
+
+template <int Q, typename T, typename S, bool ACC>
+__global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(const StepArgs<T> p)
+{
+    step_body<Q, T, S, ACC>(p, blockIdx.x);
+}
+
+// Many lattices in one launch: the block finds its lattice by binary search
+// over the block prefix and works from a shared-memory copy of that
+// lattice's arguments.
+template <int Q, typename T, typename S, bool ACC>
+__global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>()))
+    k_step_batch(const StepArgs<T> *__restrict__ table, const int *__restrict__ prefix, int n)
+{
+    __shared__ StepArgs<T> sp;
+    __shared__ int s_lid;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;  // last l with prefix[l] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(prefix + mid) <= (int)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_lid = lo;
+    }
+    __syncthreads();
+    const int lid = s_lid;
+    static_assert(sizeof(StepArgs<T>) % 16 == 0, "argument record in 16-byte words");
+    const int4 *src = reinterpret_cast<const int4 *>(table + lid);
+    int4 *dst = reinterpret_cast<int4 *>(&sp);
+    for (int k = threadIdx.x; k < (int)(sizeof(StepArgs<T>) / 16); k += blockDim.x) dst[k] = __ldg(src + k);
+    __syncthreads();
+    step_body<Q, T, S, ACC>(sp, (int)blockIdx.x - __ldg(prefix + lid));
 }
 
 // ---------------------------------------------------------------------------
@@ -783,10 +827,10 @@ __global__ void k_ref_sum(const StepArgs<T> p, float *enc0, float *enc1, float *
         s = 2;
         row = r - nrw - nrs;
     }
-    const int b0 = s == 0 ? row * p.nchunk : p.nbw + row * p.nchunk;
+    const int seg0 = (s == 0 ? 0 : p.nseg_w) + row * p.nch32;
     const int off = s == 2 ? Q + i : i;
     float sum = 0.f;
-    for (int c = 0; c < p.nchunk; ++c) sum += p.acc[(size_t)(b0 + c) * 2 * Q + off];
+    for (int c = 0; c < p.nch32; ++c) sum += p.acc[(size_t)(seg0 + c) * 2 * Q + off];
     float *enc = s == 0 ? enc0 : (s == 1 ? enc1 : enc2);
     enc[(size_t)row * kRefStride + i] = sum / (float)p.nx;
 }
@@ -845,6 +889,22 @@ cudaError_t launch_q(const void *args, int mode, int nblocks, int bx, cudaStream
         break;
     default:
         return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int Q, typename T, typename S>
+cudaError_t launch_batch_q(const void *table, const int *prefix, int n, int nblocks, int bx,
+                           bool acc, cudaStream_t s)
+{
+    const StepArgs<T> *t = static_cast<const StepArgs<T> *>(table);
+    if (acc) {
+        if constexpr (Storage<S>::kRef)
+            k_step_batch<Q, T, S, true><<<nblocks, bx, 0, s>>>(t, prefix, n);
+        else
+            return cudaErrorInvalidValue;
+    } else {
+        k_step_batch<Q, T, S, false><<<nblocks, bx, 0, s>>>(t, prefix, n);
     }
     return cudaGetLastError();
 }

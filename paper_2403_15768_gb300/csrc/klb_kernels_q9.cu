@@ -26,4 +26,21 @@ cudaError_t launch_ref_q9(const void *args, float *const enc[3], float *const de
     return launch_ref_q<9, float>(args, enc, dec, s);
 }
 
+cudaError_t launch_batch_q9(int storage, const void *table, const int *prefix, int n, int nblocks,
+                          int bx, bool acc, cudaStream_t s)
+{
+    switch (storage) {
+    case KLB_FP64:
+        return launch_batch_q<9, double, double>(table, prefix, n, nblocks, bx, acc, s);
+    case KLB_FP32:
+        return launch_batch_q<9, float, float>(table, prefix, n, nblocks, bx, acc, s);
+    case KLB_FP16_DEV:
+        return launch_batch_q<9, float, __half>(table, prefix, n, nblocks, bx, acc, s);
+    case KLB_BF16_DEV:
+        return launch_batch_q<9, float, __nv_bfloat16>(table, prefix, n, nblocks, bx, acc, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace klb

@@ -88,3 +88,88 @@ def perturbation(w: Workload, seed: int, eps: float):
     if w.kind == 9:
         eta[:, 2] = 0.0
     return w.rho0 * eps * xi, eps * eta
+
+
+def channel_sweep(n: int = 96, seed: int = 0, storage: str = "fp32", scale: float = 1.0):
+    """A design sweep of n independent D3Q19 channels: slab or pipe with
+    probability 1/2; nx uniform in [64, 512], box cross-section ny, nz uniform
+    in [16, 128] (shell included), shell uniform in [2, 8]; tau_w uniform in
+    [0.55, 1.2] (tau_e 0.6, tau_p 1.0); drive g log-uniform in [1e-7, 1e-5];
+    the couplings g_we, g_wp, g_ep, g_pc log-uniform in [1e-4, 1e-1],
+    g_ec = 0 (a fluid cell of these channels has at most two solid faces, so
+    the face-summed interface friction stays below 0.4 rho0, inside the
+    stability bound).
+    Draws from default_rng(seed) in that order, channel by channel.  A pipe's
+    radius is the largest that fits its shell in the box (at least 2); a
+    slab's fluid width is ny - 2 shell.  ``scale`` shrinks every length (for
+    quick tests)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        kind = "pipe" if rng.uniform() < 0.5 else "slab"
+        nx = int(rng.integers(64, 513))
+        ny = int(rng.integers(16, 129))
+        nz = int(rng.integers(16, 129))
+        shell = int(rng.integers(2, 9))
+        tau_w = float(rng.uniform(0.55, 1.2))
+        g = float(10 ** rng.uniform(-7, -5))
+        g_we, g_wp, g_ep, g_pc = (float(v) for v in 10 ** rng.uniform(-4, -1, 4))
+        if scale != 1.0:
+            nx, ny, nz = (max(8, int(round(v * scale))) for v in (nx, ny, nz))
+            shell = max(1, int(round(shell * scale)))
+        common = dict(name=f"sweep{seed}_{k}_{kind}", kind=19, nx=nx, ny=ny, nz=nz, shell=shell,
+                      tau=(tau_w, 0.6, 1.0), G=(g, 0.0, 0.0),
+                      couplings=(g_we, g_wp, g_ep, 0.0, g_pc), storage=storage)
+        if kind == "pipe":
+            radius = max(2, min(ny, nz) // 2 - shell)
+            ny = nz = max(ny, nz, 2 * (radius + shell))
+            common.update(ny=ny, nz=nz)
+            out.append(Workload(geom="pipe", radius=radius, **common))
+        else:
+            ny = max(ny, 2 * shell + 2)
+            common.update(ny=ny)
+            out.append(Workload(geom="slab", width=ny - 2 * shell, **common))
+    return out
+
+
+@dataclass(frozen=True)
+class Request:
+    """One design-sweep solve of a request stream: its arrival time (s after
+    the stream starts) and its channel."""
+    rid: int
+    arrival: float
+    w: Workload
+
+
+def request_stream(n: int, rate: float = 50.0, seed: int = 0, storage: str = "fp32",
+                   max_cells: int = 512 * 128 * 128, min_cells: int = 32 ** 3):
+    """n requests of a Poisson stream with ``rate`` arrivals per second.  Per
+    request, from default_rng(seed) in this order: the inter-arrival time
+    (exponential, mean 1/rate); the cell count C log-uniform in
+    [min_cells, max_cells]; the aspect a uniform in [1, 4], giving
+    ny = nz = round((C/a)^(1/3)) and nx = round(C/ny^2); slab or pipe with
+    probability 1/2; then shell, tau_w, drive and couplings drawn as in
+    channel_sweep.  The cross-section is at least 2 shell + 4 cells wide."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        c = float(np.exp(rng.uniform(np.log(min_cells), np.log(max_cells))))
+        a = float(rng.uniform(1.0, 4.0))
+        kind = "pipe" if rng.uniform() < 0.5 else "slab"
+        shell = int(rng.integers(2, 9))
+        tau_w = float(rng.uniform(0.55, 1.2))
+        g = float(10 ** rng.uniform(-7, -5))
+        g_we, g_wp, g_ep, g_pc = (float(v) for v in 10 ** rng.uniform(-4, -1, 4))
+        ny = max(int(round((c / a) ** (1.0 / 3.0))), 2 * shell + 4)
+        nx = max(1, int(round(c / ny ** 2)))
+        common = dict(name=f"req{seed}_{k}_{kind}", kind=19, nx=nx, ny=ny, nz=ny, shell=shell,
+                      tau=(tau_w, 0.6, 1.0), G=(g, 0.0, 0.0),
+                      couplings=(g_we, g_wp, g_ep, 0.0, g_pc), storage=storage)
+        if kind == "pipe":
+            w = Workload(geom="pipe", radius=ny // 2 - shell, **common)
+        else:
+            w = Workload(geom="slab", width=ny - 2 * shell, **common)
+        out.append(Request(k, t, w))
+    return out

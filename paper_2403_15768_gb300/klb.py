@@ -30,7 +30,12 @@ EXPORTS = ["klb_lattice_bytes", "klb_lattice_info", "klb_create_lattice", "klb_s
            "klb_init_equilibrium", "klb_step", "klb_observables", "klb_observables_static",
            "klb_get_field",
            "klb_get_state", "klb_set_state", "klb_get_step", "klb_species_cells",
-           "klb_destroy", "klb_last_error"]
+           "klb_destroy", "klb_last_error", "klb_batch_bytes", "klb_batch_create",
+           "klb_batch_step", "klb_batch_autotune", "klb_batch_width", "klb_batch_blocks",
+           "klb_batch_destroy", "klb_batch_last_error", "klb_server_table_bytes",
+           "klb_server_create", "klb_server_submit", "klb_server_tick", "klb_server_poll",
+           "klb_server_get_stats", "klb_server_clock", "klb_server_destroy",
+           "klb_server_last_error"]
 
 
 class klb_desc(ctypes.Structure):
@@ -74,6 +79,42 @@ class klb_info(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return klb_obs.as_dict(self)
+
+
+class klb_server_opts(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("max_resident", ctypes.c_int32),
+                ("autotune_steps", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class klb_request(ctypes.Structure):
+    _fields_ = [("desc", klb_desc), ("couplings", klb_couplings), ("tol", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("max_seconds", ctypes.c_double),
+                ("arrival", ctypes.c_double), ("id", ctypes.c_int64)]
+
+
+class klb_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("steps", ctypes.c_int64), ("sites", ctypes.c_int64), ("bytes", ctypes.c_uint64),
+                ("arrival", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("finished", ctypes.c_double), ("obs", klb_obs)]
+
+    def as_dict(self) -> dict:
+        out = {n: getattr(self, n) for n, _ in self._fields_ if n not in ("pad", "obs")}
+        out["obs"] = self.obs.as_dict()
+        return out
+
+
+class klb_server_stats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64),
+                ("finished", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("batch_forms", ctypes.c_int64), ("arena_bytes", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_uint64), ("peak_bytes_in_use", ctypes.c_uint64),
+                ("table_bytes", ctypes.c_uint64), ("site_updates", ctypes.c_double),
+                ("width", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "pad"}
 
 
 class KLBError(RuntimeError):
@@ -122,6 +163,40 @@ def load_library(path: str | None = None):
     lib.klb_destroy.argtypes = [P]
     lib.klb_last_error.restype = ctypes.c_char_p
     lib.klb_last_error.argtypes = [P]
+    lib.klb_batch_bytes.restype = SZ
+    lib.klb_batch_bytes.argtypes = [ctypes.POINTER(P), ctypes.c_int]
+    lib.klb_batch_create.restype = I32
+    lib.klb_batch_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, P, SZ, ctypes.POINTER(P)]
+    lib.klb_batch_step.restype = I32
+    lib.klb_batch_step.argtypes = [P, I64]
+    lib.klb_batch_autotune.restype = I32
+    lib.klb_batch_autotune.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.klb_batch_width.restype = ctypes.c_int
+    lib.klb_batch_width.argtypes = [P]
+    lib.klb_batch_blocks.restype = I64
+    lib.klb_batch_blocks.argtypes = [P]
+    lib.klb_batch_destroy.restype = I32
+    lib.klb_batch_destroy.argtypes = [P]
+    lib.klb_batch_last_error.restype = ctypes.c_char_p
+    lib.klb_batch_last_error.argtypes = [P]
+    lib.klb_server_table_bytes.restype = SZ
+    lib.klb_server_table_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.klb_server_create.restype = I32
+    lib.klb_server_create.argtypes = [P, SZ, P, ctypes.POINTER(klb_server_opts), ctypes.POINTER(P)]
+    lib.klb_server_submit.restype = I32
+    lib.klb_server_submit.argtypes = [P, ctypes.POINTER(klb_request)]
+    lib.klb_server_tick.restype = I32
+    lib.klb_server_tick.argtypes = [P, ctypes.POINTER(I64)]
+    lib.klb_server_poll.restype = I64
+    lib.klb_server_poll.argtypes = [P, ctypes.POINTER(klb_result), I64]
+    lib.klb_server_get_stats.restype = I32
+    lib.klb_server_get_stats.argtypes = [P, ctypes.POINTER(klb_server_stats)]
+    lib.klb_server_clock.restype = ctypes.c_double
+    lib.klb_server_clock.argtypes = [P]
+    lib.klb_server_destroy.restype = I32
+    lib.klb_server_destroy.argtypes = [P]
+    lib.klb_server_last_error.restype = ctypes.c_char_p
+    lib.klb_server_last_error.argtypes = [P]
     _lib = lib
     return lib
 
@@ -254,6 +329,132 @@ class Lattice:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _check(_lib.klb_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many lattices stepped together, one launch per step (klb_batch_*).
+    The members must share kind, storage, stream and time level."""
+
+    def __init__(self, members):
+        import torch
+
+        lib = load_library()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        self._arr = arr
+        n = lib.klb_batch_bytes(arr, len(self.members))
+        if n == 0:
+            raise KLBError(1, "these lattices cannot form a batch")
+        self.buf = torch.empty(n, dtype=torch.uint8, device=self.members[0].device)
+        self._h = ctypes.c_void_p()
+        st = lib.klb_batch_create(arr, len(self.members), ctypes.c_void_p(self.buf.data_ptr()), n,
+                                  ctypes.byref(self._h))
+        _check(st)
+
+    def _bcheck(self, st):
+        if st != 0:
+            raise KLBError(st, _lib.klb_batch_last_error(self._h).decode(errors="replace"))
+
+    def step(self, n: int = 1):
+        self._bcheck(_lib.klb_batch_step(self._h, int(n)))
+
+    def autotune(self, steps_per_candidate: int = 5) -> int:
+        w = ctypes.c_int()
+        self._bcheck(_lib.klb_batch_autotune(self._h, int(steps_per_candidate), ctypes.byref(w)))
+        return w.value
+
+    @property
+    def width(self) -> int:
+        return int(_lib.klb_batch_width(self._h))
+
+    @property
+    def blocks(self) -> int:
+        return int(_lib.klb_batch_blocks(self._h))
+
+    def active_sites(self) -> int:
+        return sum(m.active_sites() for m in self.members)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.klb_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def klb_server_table_bytes(storage: int, max_resident: int) -> int:
+    return int(load_library().klb_server_table_bytes(storage, max_resident))
+
+
+class Server:
+    """Request loop over a torch-allocated device arena of ``arena_bytes``
+    (klb_server_*): submit requests at any time, call ``tick`` to run one
+    scheduling round, ``poll`` for finished results."""
+
+    def __init__(self, arena_bytes: int, kind=KLB_D3Q19, storage="fp32", check_every=64,
+                 max_resident=128, autotune_steps=0, device="cuda", stream=None):
+        import torch
+
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise KLBError(3, "no CUDA device: the KLB library has no CPU path")
+        self.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+        self.kind = int(kind)
+        self.device = torch.device(device)
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        o = klb_server_opts(self.kind, self.storage, int(check_every), int(max_resident),
+                            int(autotune_steps), 0)
+        self._h = ctypes.c_void_p()
+        st = lib.klb_server_create(ctypes.c_void_p(self.arena.data_ptr()), int(arena_bytes),
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(o),
+                                   ctypes.byref(self._h))
+        if st != 0:
+            raise KLBError(st, lib.klb_server_last_error(None).decode(errors="replace"))
+        self._keep = {}
+
+    def _scheck(self, st):
+        if st != 0:
+            raise KLBError(st, _lib.klb_server_last_error(self._h).decode(errors="replace"))
+
+    def submit(self, desc: klb_desc, couplings, tol: float, max_steps: int, req_id: int,
+               arrival: float = -1.0, max_seconds: float = 0.0):
+        r = klb_request(desc, klb_couplings(*couplings), float(tol), int(max_steps),
+                        float(max_seconds), float(arrival), int(req_id))
+        self._scheck(_lib.klb_server_submit(self._h, ctypes.byref(r)))
+
+    def tick(self) -> int:
+        n = ctypes.c_int64()
+        self._scheck(_lib.klb_server_tick(self._h, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, max_results: int = 1024) -> list:
+        out = (klb_result * max_results)()
+        n = _lib.klb_server_poll(self._h, out, max_results)
+        return [out[k].as_dict() for k in range(n)]
+
+    def stats(self) -> dict:
+        st = klb_server_stats()
+        self._scheck(_lib.klb_server_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def clock(self) -> float:
+        return float(_lib.klb_server_clock(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.klb_server_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

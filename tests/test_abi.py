@@ -19,7 +19,7 @@ def test_library_exports_every_declared_entry_point():
     lib = klb.load_library()
     with open(os.path.join(ROOT, "include", "klb.h")) as fh:
         header = fh.read()
-    declared = set(re.findall(r"^\s*(?:klb_status|size_t|int64_t|const char \*)\s*\*?\s*(klb_\w+)\s*\(",
+    declared = set(re.findall(r"^\s*(?:klb_status|size_t|int64_t|int|double|const char \*)\s*\*?\s*(klb_\w+)\s*\(",
                               header, re.M))
     assert {"klb_create_lattice", "klb_step", "klb_observables", "klb_set_couplings"} <= declared
     for name in declared:
@@ -97,3 +97,67 @@ def test_reduced_storage_halves_the_population_footprint():
     for st in ("fp16", "bf16"):
         b16 = klb.klb_lattice_bytes(klb.desc_from_workload(w.with_(storage=st)))
         assert b16 < 0.62 * b32
+
+
+def _server(arena_bytes, storage=klb.KLB_FP32, **kw):
+    """A server over a never-dereferenced arena address: creation, submission
+    and counters are host logic and touch no device."""
+    import ctypes
+
+    lib = klb.load_library()
+    o = klb.klb_server_opts(klb.KLB_D3Q19, storage, kw.get("check_every", 64),
+                            kw.get("max_resident", 8), kw.get("autotune_steps", 0), 0)
+    h = ctypes.c_void_p()
+    st = lib.klb_server_create(ctypes.c_void_p(1 << 20), arena_bytes, None, ctypes.byref(o),
+                               ctypes.byref(h))
+    return lib, st, h
+
+
+def test_server_host_logic_without_device():
+    import ctypes
+
+    lib, st, h = _server(1 << 20, autotune_steps=20, check_every=40)
+    assert st == 1 and b"check_every" in lib.klb_server_last_error(None)
+    tb = klb.klb_server_table_bytes(klb.KLB_FP32, 8)
+    assert tb % 256 == 0 and tb > 0
+    lib, st, h = _server(tb, max_resident=8)
+    assert st == 2  # arena no larger than the table region
+    w = inputs.PIPE_D3Q19_SUB
+    need = klb.klb_lattice_bytes(klb.desc_from_workload(w))
+    lib, st, h = _server(tb + need + 256)
+    assert st == 0
+
+    def req(w, **kw):
+        return klb.klb_request(klb.desc_from_workload(w), klb.klb_couplings(*w.couplings),
+                               kw.get("tol", 1e-9), kw.get("max_steps", 1000), 0.0,
+                               kw.get("arrival", -1.0), kw.get("rid", 0))
+
+    assert lib.klb_server_submit(h, ctypes.byref(req(w))) == 0
+    assert lib.klb_server_submit(h, ctypes.byref(req(w, rid=1, arrival=5.0))) == 0
+    big = w.with_(nx=2 * w.nx)
+    assert lib.klb_server_submit(h, ctypes.byref(req(big))) == 1
+    assert b"never fit" in lib.klb_server_last_error(h)
+    assert lib.klb_server_submit(h, ctypes.byref(req(w.with_(storage="fp16")))) == 1
+    assert lib.klb_server_submit(h, ctypes.byref(req(w, tol=0.0))) == 1
+    assert lib.klb_server_submit(h, ctypes.byref(req(w, max_steps=0))) == 1
+    assert lib.klb_server_submit(h, ctypes.byref(req(w.with_(tau=(0.5, 0.6, 1.0))))) == 1
+    s = klb.klb_server_stats()
+    assert lib.klb_server_get_stats(h, ctypes.byref(s)) == 0
+    assert (s.queued, s.resident, s.finished, s.bytes_in_use) == (2, 0, 0, 0)
+    assert s.table_bytes == tb and s.arena_bytes == tb + need + 256
+    out = (klb.klb_result * 4)()
+    assert lib.klb_server_poll(h, out, 4) == 0
+    assert lib.klb_server_clock(h) >= 0.0
+    assert lib.klb_server_destroy(h) == 0
+
+
+def test_request_stream_recipe():
+    rs = inputs.request_stream(200, rate=50.0, seed=0)
+    gaps = np.diff([0.0] + [r.arrival for r in rs])
+    assert np.all(gaps > 0) and 0.015 < gaps.mean() < 0.025
+    for r in rs:
+        w = r.w
+        assert w.ny == w.nz and 32 ** 3 * 0.5 < w.nx * w.ny * w.nz < 512 * 128 * 128 * 1.5
+        info = klb.klb_lattice_info(klb.desc_from_workload(w))
+        assert info["active_sites"] > 0
+    assert {r.w.geom for r in rs} == {"slab", "pipe"}

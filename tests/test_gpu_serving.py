@@ -1,0 +1,102 @@
+"""The request loop (klb_server_*): each request's result is the same alone
+and in a mix with others admitted before, with and after it (bit for bit:
+every resident lattice advances a fixed number of steps per round and is
+checked at multiples of it since its own admission); admission respects the
+arena; step limits and non-finite states retire requests with their
+status."""
+import numpy as np
+import pytest
+
+from paper_2403_15768_gb300 import inputs, klb, serving
+
+pytestmark = pytest.mark.gpu
+
+STREAM = inputs.request_stream(7, rate=50.0, seed=5, min_cells=6 ** 3, max_cells=20 ** 3)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    klb.load_library()
+
+
+def _bytes(w):
+    return klb.klb_lattice_bytes(klb.desc_from_workload(w))
+
+
+def _run(reqs, arena, storage="fp32", check_every=20, autotune_steps=0, tol=1e-8,
+         max_steps=2000, stagger=False):
+    srv = klb.Server(arena, storage=storage, check_every=check_every, max_resident=8,
+                     autotune_steps=autotune_steps)
+    out = {}
+    pending = list(reqs)
+    it = 0
+    while pending or len(out) < len(reqs):
+        # staggered: one new request every second round
+        it += 1
+        if pending and (not stagger or it % 2 == 1):
+            r = pending.pop(0)
+            srv.submit(klb.desc_from_workload(r.w), r.w.couplings, tol, max_steps, r.rid)
+        srv.tick()
+        for res in srv.poll():
+            out[res["id"]] = res
+    stats = srv.stats()
+    srv.close()
+    return out, stats
+
+
+def _same(a, b):
+    assert a["status"] == b["status"] and a["steps"] == b["steps"]
+    for k, v in a["obs"].items():
+        w = b["obs"][k]
+        assert np.array_equal(np.asarray(v), np.asarray(w), equal_nan=True), k
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_result_alone_equals_result_in_the_mix(storage):
+    reqs = [inputs.Request(r.rid, r.arrival, r.w.with_(storage=storage)) for r in STREAM]
+    total = sum(_bytes(r.w) for r in reqs)
+    arena = total + klb.klb_server_table_bytes(klb.STORAGE[storage], 8) + 64 * 1024 * 1024
+    tol = 1e-8 if storage == "fp32" else 1e-6
+    alone = {r.rid: _run([r], arena, storage, tol=tol)[0][r.rid] for r in reqs}
+    mix, stats = _run(reqs, arena, storage, tol=tol, stagger=True, autotune_steps=2)
+    assert stats["batch_forms"] >= 3 and stats["finished"] == len(reqs)
+    assert stats["peak_bytes_in_use"] <= arena
+    for r in reqs:
+        _same(alone[r.rid], mix[r.rid])
+        assert mix[r.rid]["steps"] % 20 == 0
+    assert any(v["status"] == 0 for v in mix.values())
+
+
+def test_admission_waits_for_arena_space():
+    """An arena that holds the two largest requests only: requests queue,
+    the peak footprint stays inside the arena, and results are unchanged."""
+    sizes = sorted((_bytes(r.w) for r in STREAM), reverse=True)
+    arena = klb.klb_server_table_bytes(klb.KLB_FP32, 8) + sizes[0] + sizes[1] + 4096
+    small, stats = _run(STREAM, arena)
+    big, _ = _run(STREAM, 4 * sum(sizes))
+    assert stats["peak_bytes_in_use"] <= sizes[0] + sizes[1] + 4096
+    for r in STREAM:
+        _same(small[r.rid], big[r.rid])
+        assert small[r.rid]["admitted"] >= small[r.rid]["arrival"]
+
+
+def test_step_limit_and_unstable_requests():
+    w = STREAM[0].w
+    blow = w.with_(G=(0.3, 0.0, 0.0), tau=(0.501, 0.6, 1.0), couplings=(0.0,) * 5)
+    reqs = [inputs.Request(0, 0.0, w), inputs.Request(1, 0.0, blow)]
+    out, _ = _run(reqs, 4 * (_bytes(w) + 2 ** 26), check_every=64, tol=1e-30, max_steps=100)
+    assert out[0]["status"] == 5 and out[0]["steps"] == 128  # KLB_ETIMEOUT at the first check >= 100
+    assert out[1]["status"] == 4 and out[1]["obs"]["nonfinite"] > 0  # KLB_EUNSTABLE
+
+
+def test_replay_reports_latencies():
+    srv = klb.Server(256 * 1024 * 1024, check_every=25, max_resident=8)
+    run = serving.replay(srv, STREAM, tol=1e-8, max_steps=300)
+    s = serving.summarise(run)
+    srv.close()
+    assert s["finished"] == len(STREAM) and s["p99_s"] >= s["p50_s"] > 0 and s["mlups"] > 0
+    for r in run["results"]:
+        assert r["arrival"] <= r["admitted"] <= r["finished"]
