@@ -76,9 +76,9 @@ void *dev(const klb_lattice *L, size_t off) { return L->base + off; }
 int slot_of(int64_t m) { return (int)(((m % 3) + 3) % 3); }
 
 // Kernel arguments for the time level `st` (the step about to run, or the
-// one observed) with blocks of bx consecutive x.
+// one observed); the step kernel runs blocks of sbx threads.
 template <typename T>
-void fill_args_at(const klb_lattice *L, const HostState &st, int bx, StepArgs<T> &a)
+void fill_args_at(const klb_lattice *L, const HostState &st, int sbx, StepArgs<T> &a)
 {
     const Geometry &g = L->geo;
     const MemoryPlan &p = L->plan;
@@ -112,8 +112,10 @@ void fill_args_at(const klb_lattice *L, const HostState &st, int bx, StepArgs<T>
     }
     a.nx = g.nx;
     a.nxp = g.nxp;
-    a.nchunk = (g.nx + bx - 1) / bx;
+    a.nchunk = p.nchunk;
     a.nbw = (int)g.rows[kFluid].size() * a.nchunk;
+    a.snchunk = step_chunks(g.nx, sbx, L->desc.storage);
+    a.snbw = (int)g.rows[kFluid].size() * a.snchunk;
     a.nch32 = (g.nx + 31) / 32;
     a.nseg_w = (int)g.rows[kFluid].size() * a.nch32;
     const klb_desc &d = L->desc;
@@ -135,7 +137,7 @@ void fill_args_at(const klb_lattice *L, const HostState &st, int bx, StepArgs<T>
 template <typename T>
 void fill_args(const klb_lattice *L, StepArgs<T> &a)
 {
-    fill_args_at(L, L->st, L->plan.bx, a);
+    fill_args_at(L, L->st, L->plan.sbx, a);
 }
 
 // The host side of one step: encode generation of the output, whether the
@@ -450,7 +452,7 @@ klb_status klb_step(klb_lattice *L, int64_t nsteps)
         cudaError_t e = with_args(L, [&](void *a) {
             set_enc(L, a, sp.outgen);
             return launch(L->geo.Q, L->desc.storage, a, sp.acc ? kModeStepAcc : kModeStep,
-                          nblocks(L), L->plan.bx, L->stream);
+                          L->plan.snblocks, L->plan.sbx, L->stream);
         });
         if (e != cudaSuccess) return cuda_fail(L, e, "step kernel launch");
         advance(L->st, sp);
@@ -886,7 +888,7 @@ klb_status build_tables(klb_batch *B, int width)
             }
             advance(st, sp);
         }
-        const int chunks = (L->geo.nx + width - 1) / width;
+        const int chunks = step_chunks(L->geo.nx, width, L->desc.storage);
         prefix[m + 1] = prefix[m] + chunks * (int)(L->geo.rows[kFluid].size() + L->geo.rows[kSolid].size());
     }
     KLB_BCUDA(B, cudaStreamSynchronize(B->stream));
@@ -1067,7 +1069,7 @@ klb_status klb_batch_create(klb_lattice *const *members, int n, void *dev_buf, s
         return fail(nullptr, KLB_ECUDA, m);
     }
     int w = kBlockX;
-    for (klb_lattice *L : B->mem) w = std::min(w, L->plan.bx);
+    for (klb_lattice *L : B->mem) w = std::min(w, L->plan.sbx);
     klb_status st = build_tables(B, w);
     if (st != KLB_OK) {
         std::string m = B->err;

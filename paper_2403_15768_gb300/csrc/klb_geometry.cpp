@@ -312,6 +312,11 @@ MemoryPlan plan_memory(const Geometry &g, int storage)
     p.nchunk = (g.nx + p.bx - 1) / p.bx;
     p.nblocks_w = (int)nr[kFluid] * p.nchunk;
     p.nblocks_s = (int)nr[kSolid] * p.nchunk;
+    {
+        const int xt = (g.nx + step_cells(storage) - 1) / step_cells(storage);  // threads per row
+        p.sbx = std::min(kBlockX, std::max(32, (xt + 31) / 32 * 32));
+        p.snblocks = (int)(nr[kFluid] + nr[kSolid]) * step_chunks(g.nx, p.sbx, storage);
+    }
     p.partials = take(sizeof(double) * kNumSums * (size_t)(p.nblocks_w + p.nblocks_s));
     p.sums = take(sizeof(double) * kNumSums);
     p.field_bytes = ts * 4 * (nr[kFluid] + 2 * nr[kSolid]) * g.nxp;

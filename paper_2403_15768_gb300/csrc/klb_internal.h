@@ -91,7 +91,8 @@ struct MemoryPlan {
     size_t ref_bytes[3];
     size_t acc, acc_bytes;
     size_t total;
-    int nblocks_w, nblocks_s, nchunk, bx;
+    int nblocks_w, nblocks_s, nchunk, bx;  // one cell per thread (observe, field, init)
+    int sbx, snblocks;                     // step kernel: threads per block, blocks
 };
 MemoryPlan plan_memory(const Geometry &g, int storage);
 
@@ -102,6 +103,17 @@ MemoryPlan plan_memory(const Geometry &g, int storage);
 constexpr int kRefStride = 20;
 constexpr int kRefEvery = 32;
 constexpr float kFp16Scale = 1048576.0f;  // 2^20
+
+// Cells per thread of the step kernel: two adjacent x with packed FP32
+// arithmetic, one in FP64.
+inline int step_cells(int storage) { return storage == KLB_FP64 ? 1 : 2; }
+
+// Step-kernel blocks of a lattice with nx x-cells, nrows rows, sbx threads.
+inline int step_chunks(int nx, int sbx, int storage)
+{
+    const int xb = sbx * step_cells(storage);
+    return (nx + xb - 1) / xb;
+}
 
 inline bool reduced_storage(int storage) { return storage == KLB_FP16_DEV || storage == KLB_BF16_DEV; }
 inline size_t storage_bytes(int storage)
@@ -120,6 +132,7 @@ struct alignas(16) StepArgs {
     const T *U1[2], *U2[2], *U3[2];  // lagged velocities u(n-1), u(n-2), u(n-3)
     T *U0[2];                        // u(n) written here (step mode)
     int nx, nxp, nchunk, nbw;        // nchunk = x chunks of blockDim.x per row; nbw = water blocks
+    int snchunk, snbw;               // the same for the step kernel (step_cells x per thread)
     int nch32, nseg_w;               // 32-wide x segments per row; water segments
     int n_rows[2], n_slots[2];
     T rho0, om[3], G[3];

@@ -655,16 +655,16 @@ static_assert(offsetof(RowInfo, xm) == 19 * 4 && offsetof(RowInfo, xp) == 20 * 4
 template <typename T, typename S>
 constexpr int step_min_blocks()
 {
-    return sizeof(T) == 8 ? 4 : (Storage<S>::kRef ? 6 : 8);
+    return sizeof(T) == 8 ? 4 : (Storage<S>::kRef ? 4 : 4);
 }
 
 template <int Q, typename T, typename S, bool ACC>
 __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
 {
-    const bool water = b < p.nbw;
-    const int bb = water ? b : b - p.nbw;
-    const int row = bb / p.nchunk;
-    int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
+    const bool water = b < p.snbw;
+    const int bb = water ? b : b - p.snbw;
+    const int row = bb / p.snchunk;
+    int x = (bb - row * p.snchunk) * blockDim.x + threadIdx.x;
     const int x_lane = x;
     const bool live = x < p.nx;
     if constexpr (!ACC) {
@@ -766,10 +766,26 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
     }
 }
 
+}  // namespace klb
+
+#include "klb_step_pair.cuh"
+
+namespace klb {
+
+// FP32 arithmetic: two cells per thread (klb_step_pair.cuh); FP64: one.
+template <int Q, typename T, typename S, bool ACC>
+__device__ __forceinline__ void step_cells_body(const StepArgs<T> &p, int b)
+{
+    if constexpr (sizeof(T) == 4)
+        step_body2<Q, S, ACC>(p, b);
+    else
+        step_body<Q, T, S, ACC>(p, b);
+}
+
 template <int Q, typename T, typename S, bool ACC>
 __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(const StepArgs<T> p)
 {
-    step_body<Q, T, S, ACC>(p, blockIdx.x);
+    step_cells_body<Q, T, S, ACC>(p, blockIdx.x);
 }
 
 // Many lattices in one launch: the block finds its lattice by binary search
@@ -799,7 +815,7 @@ __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>()))
     int4 *dst = reinterpret_cast<int4 *>(&sp);
     for (int k = threadIdx.x; k < (int)(sizeof(StepArgs<T>) / 16); k += blockDim.x) dst[k] = __ldg(src + k);
     __syncthreads();
-    step_body<Q, T, S, ACC>(sp, (int)blockIdx.x - __ldg(prefix + lid));
+    step_cells_body<Q, T, S, ACC>(sp, (int)blockIdx.x - __ldg(prefix + lid));
 }
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,462 @@
+// Step body with two cells per thread and packed FP32 arithmetic (the f32x2
+// add, multiply and fused multiply-add of sm_100 and later: one instruction
+// computes the same operation for both cells, each element rounded as its
+// scalar counterpart would be).  Used for FP32 arithmetic (FP32, FP16 and
+// BF16 storage); FP64 keeps one cell per thread.
+//
+// A thread owns the adjacent cells x0 = 2t and x0 + 1 of one row, so the
+// populations of both come from one aligned 8-byte (FP32) or 4-byte (16-bit)
+// word wherever the direction does not move along x; an x-moving direction
+// pulls its two cells from x0 - 1, x0 (c_x = +1) or x0 + 1, x0 + 2
+// (c_x = -1) with two scalar loads.  Both cells share the row's table, its
+// references and its index arithmetic.  The second cell of the last pair
+// of an odd row lies in the row padding: it is computed from in-bounds
+// values and never stored or summed.
+//
+// The arithmetic is that of step_body (moments, interface friction from
+// lagged velocities, trapezoidal electron-phonon friction and sinks, Guo
+// velocity, BGK + Guo collision with the FP32 moment fix-up), with the
+// collision evaluated per pair of opposite directions: for c_ibar = -c_i the
+// equilibrium and forcing terms split into parts even and odd in c,
+//   teq = e0 + 4.5 rho (c.u)^2  +-  3 rho (c.u),
+//   tF  = -3 u.F + 9 (c.u)(c.F) +-  3 (c.F),
+// computed once per pair.
+
+#pragma once
+
+namespace klb {
+
+__device__ __forceinline__ float2 b2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once (b * -1 is exact).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, b2(-1.f), a); }
+
+// Pair access to the storage types.
+template <typename S> struct Pair;
+template <> struct Pair<float> {
+    __device__ static float2 load2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    __device__ static float load1(const float *p) { return __ldg(p); }
+    __device__ static void store2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+    __device__ static void store1(float *p, float v) { *p = v; }
+};
+template <> struct Pair<__half> {
+    __device__ static float2 load2(const __half *p)
+    {
+        return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+    }
+    __device__ static float load1(const __half *p) { return Storage<__half>::load(p); }
+    __device__ static void store2(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
+    __device__ static void store1(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Pair<__nv_bfloat16> {
+    __device__ static float2 load2(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+    }
+    __device__ static float load1(const __nv_bfloat16 *p) { return Storage<__nv_bfloat16>::load(p); }
+    __device__ static void store2(__nv_bfloat16 *p, float2 v)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+    }
+    __device__ static void store1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+struct Cell2 {
+    float2 drho;
+    float2 u[3];
+    float2 F[3];
+};
+
+// Source columns of the two cells for the three x shifts.
+struct Cols {
+    int x0, pm_a, pp_a, pp_b;
+};
+
+template <int Q>
+__host__ __device__ constexpr int opp(int i)
+{
+    return dir_index<Q>(-cx<Q>(i), -cy<Q>(i), -cz<Q>(i));
+}
+
+// c_i . v for a pair of cells.
+template <int Q>
+__device__ __forceinline__ float2 cdot2(int i, const float2 v[3])
+{
+    const int c[3] = {cx<Q>(i), cy<Q>(i), cz<Q>(i)};
+    float2 r = b2(0.f);
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] == 0) continue;
+        if (!any)
+            r = c[a] > 0 ? v[a] : make_float2(-v[a].x, -v[a].y);
+        else
+            r = c[a] > 0 ? add2(r, v[a]) : sub2(r, v[a]);
+        any = true;
+    }
+    return r;
+}
+
+template <int Q>
+__device__ __forceinline__ float2 cmoment2(int a, const float2 g[Q])
+{
+    float2 r = b2(0.f);
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int c = a == 0 ? cx<Q>(i) : (a == 1 ? cy<Q>(i) : cz<Q>(i));
+        if (c == 0) continue;
+        if (!any)
+            r = c > 0 ? g[i] : make_float2(-g[i].x, -g[i].y);
+        else
+            r = c > 0 ? add2(r, g[i]) : sub2(r, g[i]);
+        any = true;
+    }
+    return r;
+}
+
+template <int Q>
+__device__ __forceinline__ void moments2(const float2 g[Q], float2 &drho, float2 j[3])
+{
+    drho = g[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) drho = add2(drho, g[i]);
+    j[0] = cmoment2<Q>(0, g);
+    j[1] = cmoment2<Q>(1, g);
+    j[2] = Q == 19 ? cmoment2<Q>(2, g) : b2(0.f);
+}
+
+// Pull direction i of both cells.  SHIFT is the x shift of the direction's
+// source (+1: from x - 1, -1: from x + 1, 0: none).
+template <typename S, bool REF>
+__device__ __forceinline__ float2 pull_dir(const S *__restrict__ in, int src, int shift, const Cols &X,
+                                           float ref, float inv)
+{
+    const S *q = in + src;
+    float2 v;
+    if (shift == 0)
+        v = Pair<S>::load2(q + X.x0);
+    else if (shift > 0)
+        v = make_float2(Pair<S>::load1(q + X.pm_a), Pair<S>::load1(q + X.x0));
+    else
+        v = make_float2(Pair<S>::load1(q + X.pp_a), Pair<S>::load1(q + X.pp_b));
+    if constexpr (REF) v = fma2(v, b2(inv), b2(ref));
+    return v;
+}
+
+template <int Q, typename S>
+__device__ __forceinline__ void pull_row2(const S *__restrict__ in, const int src[Q], uint32_t xm,
+                                          uint32_t xp, bool xbounce, const Cols &X, const float *dec,
+                                          float inv, float2 g[Q])
+{
+    constexpr bool REF = Storage<S>::kRef;
+    if (!xbounce) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            g[i] = pull_dir<S, REF>(in, src[i], cx<Q>(i), X, REF ? __ldg(dec + i) : 0.f, inv);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int sh = ((xm >> i) & 1u) ? 1 : (((xp >> i) & 1u) ? -1 : 0);
+            g[i] = pull_dir<S, REF>(in, src[i], sh, X, REF ? __ldg(dec + i) : 0.f, inv);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+
+__device__ __forceinline__ float2 lagged2(const float *U1, const float *U2, int idx)
+{
+    return mul2(b2(0.5f), add2(ld2(U1 + idx), ld2(U2 + idx)));
+}
+
+__device__ __forceinline__ float2 rcp2(float2 r) { return make_float2(1.f / r.x, 1.f / r.y); }
+
+template <int Q>
+__device__ __forceinline__ void water_math2(const StepArgs<float> &p, const RowInfo &R, int x0,
+                                            const float2 g[Q], Cell2 &c, float2 j[3])
+{
+    moments2<Q>(g, c.drho, j);
+    c.F[0] = b2(p.G[0]);
+    c.F[1] = b2(p.G[1]);
+    c.F[2] = b2(p.G[2]);
+    const int slot = R.slot;
+    if (slot >= 0) {
+        const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
+        const int nface = R.nface;
+        const float *Uw1 = p.U1[kFluid], *Uw2 = p.U2[kFluid], *Us1 = p.U1[kSolid], *Us2 = p.U2[kSolid];
+        for (int a = 0; a < 3; ++a) {
+            const float2 uw = lagged2(Uw1, Uw2, (a * ns_w + slot) * nxp + x0);
+            float2 f = b2(0.f);
+            for (int k = 0; k < nface; ++k) {
+                const int q = R.partner[k];
+                const float2 de = sub2(uw, lagged2(Us1, Us2, (a * ns_s + q) * nxp + x0));
+                const float2 dp = sub2(uw, lagged2(Us1, Us2, ((a + 3) * ns_s + q) * nxp + x0));
+                f = sub2(f, fma2(b2(p.g_we), de, mul2(b2(p.g_wp), dp)));
+            }
+            c.F[a] = add2(c.F[a], f);
+        }
+    }
+    const float2 rinv = rcp2(add2(b2(p.rho0), c.drho));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c.u[a] = mul2(fma2(b2(0.5f), c.F[a], j[a]), rinv);
+}
+
+template <int Q>
+__device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const RowInfo &R, int x0,
+                                            const float2 ge[Q], const float2 gp[Q], Cell2 &ce,
+                                            Cell2 &cp, float2 je[3], float2 jp[3])
+{
+    moments2<Q>(ge, ce.drho, je);
+    moments2<Q>(gp, cp.drho, jp);
+    float2 Fe[3] = {b2(0.f), b2(0.f), b2(0.f)}, Fp[3] = {b2(0.f), b2(0.f), b2(0.f)};
+    const int slot = R.slot;
+    if (slot >= 0) {
+        const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
+        const int nface = R.nface;
+        const float *Uw1 = p.U1[kFluid], *Uw2 = p.U2[kFluid], *Us1 = p.U1[kSolid], *Us2 = p.U2[kSolid];
+        for (int a = 0; a < 3; ++a) {
+            const float2 ue = lagged2(Us1, Us2, (a * ns_s + slot) * nxp + x0);
+            const float2 up = lagged2(Us1, Us2, ((a + 3) * ns_s + slot) * nxp + x0);
+            float2 fe = b2(0.f), fp = b2(0.f);
+            for (int k = 0; k < nface; ++k) {
+                const float2 uw = lagged2(Uw1, Uw2, (a * ns_w + R.partner[k]) * nxp + x0);
+                fe = fma2(b2(p.g_we), sub2(uw, ue), fe);
+                fp = fma2(b2(p.g_wp), sub2(uw, up), fp);
+            }
+            Fe[a] = fe;
+            Fp[a] = fp;
+        }
+    }
+    // (a + k + se) ue - k up = Je,  -k ue + (b + k + sp) up = Jp.
+    const float k = 0.5f * p.g_ep, se = 0.5f * p.g_ec, sp = 0.5f * p.g_pc;
+    const float2 A = add2(add2(b2(p.rho0), ce.drho), b2(k + se));
+    const float2 B = add2(add2(b2(p.rho0), cp.drho), b2(k + sp));
+    const float2 Dinv = rcp2(sub2(mul2(A, B), b2(k * k)));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float2 Je = fma2(b2(0.5f), Fe[a], je[a]);
+        const float2 Jp = fma2(b2(0.5f), Fp[a], jp[a]);
+        const float2 ue = mul2(fma2(B, Je, mul2(b2(k), Jp)), Dinv);
+        const float2 up = mul2(fma2(A, Jp, mul2(b2(k), Je)), Dinv);
+        ce.u[a] = ue;
+        cp.u[a] = up;
+        const float2 d = sub2(ue, up);
+        ce.F[a] = sub2(sub2(Fe[a], mul2(b2(p.g_ep), d)), mul2(b2(p.g_ec), ue));
+        cp.F[a] = sub2(fma2(b2(p.g_ep), d, Fp[a]), mul2(b2(p.g_pc), up));
+    }
+}
+
+// BGK + Guo collision of both cells, per pair of opposite directions, then
+// the FP32 fix-up of mass and momentum (see collide).  g is left holding g*.
+template <int Q>
+__device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const float2 j[3], float rho0,
+                                         float om)
+{
+    const float2 rho = add2(b2(rho0), c.drho);
+    const float2 uu = fma2(c.u[2], c.u[2], fma2(c.u[1], c.u[1], mul2(c.u[0], c.u[0])));
+    const float2 uF = fma2(c.u[2], c.F[2], fma2(c.u[1], c.F[1], mul2(c.u[0], c.F[0])));
+    const float2 e0 = fma2(mul2(b2(-1.5f), rho), uu, c.drho);
+    const float2 r45 = mul2(b2(4.5f), rho);
+    const float2 m3uF = mul2(b2(-3.f), uF);
+    const float om1 = 1.f - om, fo = 1.f - 0.5f * om;
+    {
+        const float w = float(wt<Q>(0));
+        g[0] = fma2(b2(om1), g[0], fma2(b2(om * w), e0, mul2(b2(fo * w), m3uF)));
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (opp<Q>(i) < i) continue;
+        const int ib = opp<Q>(i);
+        const float w = float(wt<Q>(i));
+        const float2 cu = cdot2<Q>(i, c.u);
+        const float2 cF = cdot2<Q>(i, c.F);
+        // even parts: e0 + 4.5 rho cu^2 and -3 u.F + 9 cu cF
+        const float2 se = fma2(r45, mul2(cu, cu), e0);
+        const float2 sf = fma2(b2(9.f), mul2(cu, cF), m3uF);
+        const float2 S = fma2(b2(om * w), se, mul2(b2(fo * w), sf));
+        // odd parts: 3 rho cu and 3 cF
+        const float2 A = fma2(mul2(b2(3.f * om * w), rho), cu, mul2(b2(3.f * fo * w), cF));
+        g[i] = fma2(b2(om1), g[i], add2(S, A));
+        g[ib] = fma2(b2(om1), g[ib], sub2(S, A));
+    }
+    float2 m = g[0];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) m = add2(m, g[i]);
+    const float2 px = cmoment2<Q>(0, g), py = cmoment2<Q>(1, g);
+    g[0] = add2(g[0], sub2(c.drho, m));
+    const float2 hx = mul2(b2(0.5f), sub2(add2(j[0], c.F[0]), px));
+    const float2 hy = mul2(b2(0.5f), sub2(add2(j[1], c.F[1]), py));
+    g[dir_index<Q>(1, 0, 0)] = add2(g[dir_index<Q>(1, 0, 0)], hx);
+    g[dir_index<Q>(-1, 0, 0)] = sub2(g[dir_index<Q>(-1, 0, 0)], hx);
+    g[dir_index<Q>(0, 1, 0)] = add2(g[dir_index<Q>(0, 1, 0)], hy);
+    g[dir_index<Q>(0, -1, 0)] = sub2(g[dir_index<Q>(0, -1, 0)], hy);
+    if (Q == 19) {
+        const float2 pz = cmoment2<Q>(2, g);
+        const float2 hz = mul2(b2(0.5f), sub2(add2(j[2], c.F[2]), pz));
+        g[dir_index<Q>(0, 0, 1)] = add2(g[dir_index<Q>(0, 0, 1)], hz);
+        g[dir_index<Q>(0, 0, -1)] = sub2(g[dir_index<Q>(0, 0, -1)], hz);
+    }
+}
+
+// Store g* of both cells (only the first when the second is padding),
+// encoded against the row's references for 16-bit storage:
+// (g - ref) * scale = fma(g, scale, -ref * scale) exactly, scale being a
+// power of two.
+template <int Q, typename S>
+__device__ __forceinline__ void store_pair(const float2 g[Q], S *__restrict__ out, int row_stride,
+                                           int base, bool both, const float *enc, float scale)
+{
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        float2 v = g[i];
+        if constexpr (Storage<S>::kRef) v = fma2(v, b2(scale), b2(-__ldg(enc + i) * scale));
+        S *q = out + i * row_stride + base;
+        if (both)
+            Pair<S>::store2(q, v);
+        else
+            Pair<S>::store1(q, v.x);
+    }
+}
+
+__device__ __forceinline__ void store_u2(float *q, float2 v, bool both)
+{
+    if (both)
+        *reinterpret_cast<float2 *>(q) = v;
+    else
+        *q = v.x;
+}
+
+// x-sums over the 32-wide segment of a half warp (16 threads, 32 cells) of
+// NV pair values, written by lanes 0 and 16.
+template <int NV>
+__device__ __forceinline__ void halfwarp_xsum(const float2 (&v)[NV], float *out_lo, float *out_hi,
+                                              bool lo_ok, bool hi_ok)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float s = v[k].x + v[k].y;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && lo_ok) out_lo[k] = s;
+        if (lane == 16 && hi_ok) out_hi[k] = s;
+    }
+}
+
+template <int Q, typename S, bool ACC>
+__device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
+{
+    const bool water = b < p.snbw;
+    const int bb = water ? b : b - p.snbw;
+    const int row = bb / p.snchunk;
+    const int xt = (bb - row * p.snchunk) * blockDim.x + threadIdx.x;
+    const int x_first = 2 * xt;
+    const bool live = x_first < p.nx;
+    if constexpr (!ACC) {
+        if (!live) return;  // no warp-wide operation follows
+    }
+    Cols X;
+    X.x0 = live ? x_first : 0;  // a dead thread of an accumulating pass computes cells 0, 1
+    const bool both = X.x0 + 1 < p.nx && live;
+    X.pm_a = X.x0 == 0 ? p.nx - 1 : X.x0 - 1;
+    X.pp_a = X.x0 + 1 >= p.nx ? 0 : X.x0 + 1;
+    X.pp_b = X.x0 + 2 >= p.nx ? 0 : X.x0 + 2;
+    const int nxp = p.nxp;
+    const float inv = p.inv_scale, sc = p.scale;
+
+    const RowInfo &R = p.rows[water ? kFluid : kSolid][row];
+    const int4 *t4 = reinterpret_cast<const int4 *>(&R);
+    int src[20];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        const int4 q = __ldg(t4 + v);
+        src[4 * v] = q.x;
+        src[4 * v + 1] = q.y;
+        src[4 * v + 2] = q.z;
+        src[4 * v + 3] = q.w;
+    }
+    const uint32_t xm = (uint32_t)src[19];
+    const int4 q5 = __ldg(t4 + 5);  // xp, slot, nface, partner[0]
+    const int4 q7 = __ldg(t4 + 7);  // flags
+    const uint32_t xp = (uint32_t)q5.x;
+    const bool xbounce = (q7.x & kXBounce) != 0;
+
+    // ACC segments: half warp h of this warp covers x from seg_x0 + 32 h.
+    int seg_lo = -1, seg_hi = -1;
+    if constexpr (ACC) {
+        const int lane = threadIdx.x & 31;
+        const int xw = x_first - 2 * lane;  // first x of the warp
+        const int base = (water ? 0 : p.nseg_w) + row * p.nch32 + xw / 32;
+        if (xw < p.nx) seg_lo = base;
+        if (xw + 32 < p.nx) seg_hi = base + 1;
+    }
+
+    if (water) {
+        float2 g[Q], j[3];
+        Cell2 c;
+        pull_row2<Q, S>(static_cast<const S *>(p.in[0]), src, xm, xp, xbounce, X,
+                        ref_row<float, S>(p.dec_in[0], row), inv, g);
+        water_math2<Q>(p, R, X.x0, g, c, j);
+        if (q5.y >= 0 && live) {
+            const int ns = p.n_slots[kFluid];
+            for (int a = 0; a < 3; ++a) store_u2(p.U0[kFluid] + (a * ns + q5.y) * nxp + X.x0, c.u[a], both);
+        }
+        collide2<Q>(g, c, j, p.rho0, p.om[0]);
+        if (live)
+            store_pair<Q, S>(g, static_cast<S *>(p.out[0]), p.n_rows[kFluid] * nxp, row * nxp + X.x0, both,
+                             ref_row<float, S>(p.enc_out[0], row), sc);
+        if constexpr (ACC) {
+            float2 acc[2 * Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                acc[i] = make_float2(live ? g[i].x : 0.f, both ? g[i].y : 0.f);
+                acc[Q + i] = b2(0.f);
+            }
+            halfwarp_xsum<2 * Q>(acc, p.acc + (size_t)seg_lo * 2 * Q, p.acc + (size_t)seg_hi * 2 * Q,
+                                 seg_lo >= 0, seg_hi >= 0);
+        }
+        return;
+    }
+
+    float2 ge[Q], gp[Q], je[3], jp[3];
+    Cell2 ce, cp;
+    pull_row2<Q, S>(static_cast<const S *>(p.in[1]), src, xm, xp, xbounce, X,
+                    ref_row<float, S>(p.dec_in[1], row), inv, ge);
+    pull_row2<Q, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, X,
+                    ref_row<float, S>(p.dec_in[2], row), inv, gp);
+    solid_math2<Q>(p, R, X.x0, ge, gp, ce, cp, je, jp);
+    if (q5.y >= 0 && live) {
+        const int ns = p.n_slots[kSolid];
+        for (int a = 0; a < 3; ++a) {
+            store_u2(p.U0[kSolid] + (a * ns + q5.y) * nxp + X.x0, ce.u[a], both);
+            store_u2(p.U0[kSolid] + ((a + 3) * ns + q5.y) * nxp + X.x0, cp.u[a], both);
+        }
+    }
+    const int stride = p.n_rows[kSolid] * nxp, base = row * nxp + X.x0;
+    collide2<Q>(ge, ce, je, p.rho0, p.om[1]);
+    if (live)
+        store_pair<Q, S>(ge, static_cast<S *>(p.out[1]), stride, base, both,
+                         ref_row<float, S>(p.enc_out[1], row), sc);
+    float2 acc[ACC ? 2 * Q : 1];
+    if constexpr (ACC) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc[i] = make_float2(live ? ge[i].x : 0.f, both ? ge[i].y : 0.f);
+    }
+    pull_row2<Q, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, X,
+                    ref_row<float, S>(p.dec_in[2], row), inv, gp);
+    collide2<Q>(gp, cp, jp, p.rho0, p.om[2]);
+    if (live)
+        store_pair<Q, S>(gp, static_cast<S *>(p.out[2]), stride, base, both,
+                         ref_row<float, S>(p.enc_out[2], row), sc);
+    if constexpr (ACC) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc[Q + i] = make_float2(live ? gp[i].x : 0.f, both ? gp[i].y : 0.f);
+        halfwarp_xsum<2 * Q>(acc, p.acc + (size_t)seg_lo * 2 * Q, p.acc + (size_t)seg_hi * 2 * Q,
+                             seg_lo >= 0, seg_hi >= 0);
+    }
+}
+
+}  // namespace klb
