@@ -1,16 +1,30 @@
 """Benchmark of the three-species KLB hot path on GB300.
 
-Workload: the D3Q19 FP32 nanotube (512 x 128 x 128 box, staircase pipe of
-radius 48, 6-cell solid shell, seeded couplings).  One benchmark step is one
-check interval of the solver: 100 fused lattice steps (stream + collide +
-interface coupling of water, electrons and phonons) followed by the FP64
-observation pass (flow rate, slip length, masses, momenta, residual).
+Default workload: the D3Q19 FP32 nanotube (512 x 128 x 128 box, staircase
+pipe of radius 48, 6-cell solid shell, seeded couplings).  One benchmark step
+is one check interval of the solver: 100 fused lattice steps (stream +
+collide + interface coupling of water, electrons and phonons) followed by
+the FP64 observation pass (flow rate, slip length, masses, momenta,
+residual).
+
+Other workloads (--workload):
+  nanotube_large_{fp32,fp16,bf16}  the nanotube scaled to 768 x 192 x 192
+      (radius 72, shell 9), populations in FP32 or as 16-bit differences
+      from per-row references; same step as the default.
+  sweep_{fp32,fp16}  96 seeded channels of a design sweep in one batch (one
+      launch per lattice step, graph replay, autotuned block width); one
+      benchmark step = 384 lattice steps of every channel + the observation
+      pass of every channel.
+  serving_{fp32,fp16}  a seeded Poisson stream of design-sweep requests
+      replayed against the request loop (--steps = requests); reports
+      aggregate MLUPS and p50/p99 time to solution.
 
 Metric: MLUPS = active lattice sites (fluid + solid cells) updated per
 second, whole job.  With N GPUs (torchrun) every rank runs its own replica
 (independent channels of a design sweep: weak scaling, no data exchange).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload NAME]
 """
 from __future__ import annotations
 
@@ -42,7 +56,7 @@ def _peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("klb_kernels.cuh", "klb_internal.h"):
+    for f in ("klb_kernels.cuh", "klb_step_pair.cuh", "klb_internal.h"):
         with open(os.path.join(ROOT, "paper_2403_15768_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -182,7 +196,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+STORAGE_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
+
+
 def run(args):
+    if args.workload.startswith("sweep_"):
+        return run_sweep(args)
+    if args.workload.startswith("serving_"):
+        return run_serving(args)
     import torch
 
     from paper_2403_15768_gb300 import inputs, klb
@@ -190,13 +211,16 @@ def run(args):
     rank, local, world, dist = _dist_setup(args.gpus)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = inputs.PIPE_D3Q19_FP32
+    if args.workload == "nanotube":
+        w = inputs.PIPE_D3Q19_FP32
+    else:
+        w = inputs.PIPE_D3Q19_LARGE.with_(storage=args.workload.rsplit("_", 1)[1])
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         lat = klb.lattice_from_workload(w, device=dev, stream=stream)
     sites = lat.active_sites()
     species_cells = sum(lat.species_cells(s) for s in range(3))
-    bytes_per_launch = species_cells * 2 * 19 * 4  # read + write of every population, FP32
+    bytes_per_launch = species_cells * 2 * 19 * STORAGE_BYTES[w.storage]  # read + write of every population
 
     def interval():
         lat.step(LATTICE_STEPS_PER_STEP)
@@ -260,16 +284,18 @@ def run(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": w.name, "lattice": "D3Q19", "box": [w.nx, w.ny, w.nz],
+        "config": {"workload": w.name, "lattice": "D3Q19", "storage": w.storage,
+                   "box": [w.nx, w.ny, w.nz],
                    "radius": w.radius, "shell": w.shell, "active_sites": sites,
                    "species_cells": species_cells,
                    "lattice_steps_per_step": LATTICE_STEPS_PER_STEP,
                    "observables_per_step": 1, "parallelism": f"replicas x{world}",
-                   "l2": "working set 1.73 GB per GPU > 129 MB L2, no flush needed",
+                   "l2": f"working set {lat.nbytes / 1e9:.2f} GB per GPU > 129 MB L2, no flush needed",
                    "couplings": list(w.couplings)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": _ncu_traffic(),
-                     "kernel": "k_step<19,float>", "peak_source": peak_kind,
+                     "frac": achieved / peak,
+                     "traffic": _ncu_traffic() if args.workload == "nanotube" else None,
+                     "kernel": f"k_step<19,float,{w.storage}>", "peak_source": peak_kind,
                      "bytes_per_launch": bytes_per_launch, "launch_ms": step_kernel_ms},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 40,
                 "d2h_bytes_per_step": 144},
@@ -285,13 +311,188 @@ def run(args):
         dist.destroy_process_group()
 
 
+SWEEP_STEPS = 384  # lattice steps per benchmark step of a sweep: one 16-bit period
+
+
+def _sweep_bytes(lats, storage):
+    return sum(sum(l.species_cells(s) for s in range(3)) for l in lats) * 2 * 19 * STORAGE_BYTES[storage]
+
+
+def run_sweep(args):
+    """96 channels of a design sweep advanced as one batch."""
+    import torch
+
+    from paper_2403_15768_gb300 import inputs, klb
+
+    rank, local, world, dist = _dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    storage = args.workload.split("_", 1)[1]
+    ws = inputs.channel_sweep(96, seed=rank, storage=storage)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        lats = [klb.lattice_from_workload(w, device=dev, stream=stream) for w in ws]
+        batch = klb.Batch(lats)
+        width = batch.autotune(steps_per_candidate=8)
+    sites = sum(l.active_sites() for l in lats)
+    bytes_per_launch = _sweep_bytes(lats, storage)
+
+    def interval():
+        batch.step(SWEEP_STEPS)
+        return [l.observables() for l in lats]
+
+    with torch.cuda.stream(stream):
+        batch.step((-lats[0].nstep) % SWEEP_STEPS)  # start the timed steps at a period boundary
+        for _ in range(args.warmup):
+            interval()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk, torch.cuda.stream(stream):
+        barrier()
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            batch.step(SWEEP_STEPS)
+            ev[k][1].record(stream)
+            obs = [l.observables() for l in lats]
+        t_end.record(stream)
+        barrier()
+    ms = t_start.elapsed_time(t_end)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev) / (args.steps * SWEEP_STEPS)
+
+    cp_host = [torch.tensor(w.couplings, dtype=torch.float64).pin_memory() for w in ws]
+    with torch.cuda.stream(stream):
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for l, c in zip(lats, cp_host):
+                l.set_couplings(*c.tolist())
+            batch.step(SWEEP_STEPS)
+            obs_e2e = [l.observables() for l in lats]
+        barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    if dist is not None:
+        t = torch.tensor([ms, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    updates = sites * SWEEP_STEPS * args.steps * world
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / (step_ms * 1e-3) / 1e9
+    line = {
+        "metric": "MLUPS", "value": updates / (ms * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"design sweep of 96 D3Q19 channels (seed = rank), {storage}",
+                   "storage": storage, "channels": len(lats), "active_sites": sites,
+                   "lattice_steps_per_step": SWEEP_STEPS, "block_width": width,
+                   "blocks_per_launch": batch.blocks, "parallelism": f"replicas x{world}",
+                   "l2": f"working set {sum(l.nbytes for l in lats) / 1e9:.1f} GB > 129 MB L2, no flush needed"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": f"k_step_batch<19,float,{storage}>", "peak_source": peak_kind,
+                     "bytes_per_launch": bytes_per_launch, "launch_ms": step_ms},
+        "e2e": {"value": updates / (e2e_ms * 1e-3) / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 40 * len(lats), "d2h_bytes_per_step": 144 * len(lats)},
+        "gpu_launches": args.steps * (SWEEP_STEPS + 2 * len(lats) +
+                                      (2 * len(lats) * SWEEP_STEPS // 32 if storage != "fp32" else 0)),
+        "clocks": clk.summary(),
+        "observables": {"flow_rate_first3": [o["flow_rate"] for o in obs[:3]],
+                        "e2e_step": obs_e2e[0]["step"]},
+    }
+    if world == 1:
+        line["cpu_baseline"] = _cpu_baseline(inputs.PIPE_D3Q19_FP32)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_serving(args):
+    """A Poisson stream of design-sweep requests (50 per second, seeded)
+    replayed against the request loop; --steps requests, --warmup requests
+    of a warm-up replay."""
+    import torch
+
+    from paper_2403_15768_gb300 import inputs, klb, serving
+
+    rank, local, world, dist = _dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    storage = args.workload.split("_", 1)[1]
+    tol = 1e-9 if storage == "fp32" else 1e-7
+    max_steps = 20000
+    arena = 150 * 10 ** 9
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        srv = klb.Server(arena, storage=storage, check_every=100, max_resident=128, device=dev,
+                         stream=stream)
+        if args.warmup:
+            warm = inputs.request_stream(args.warmup, rate=50.0, seed=1000 + rank, storage=storage,
+                                         max_cells=64 ** 3)
+            serving.replay(srv, warm, tol=tol, max_steps=2000)
+        reqs = inputs.request_stream(args.steps, rate=50.0, seed=rank, storage=storage)
+        with ClockSampler(local) as clk:
+            run = serving.replay(srv, reqs, tol=tol, max_steps=max_steps)
+    summ = serving.summarise(run)
+    srv.close()
+    if dist is not None:
+        t = torch.tensor([summ["makespan_s"], summ["site_updates"]], device=dev, dtype=torch.float64)
+        mk = t.clone()
+        dist.all_reduce(mk, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        summ["makespan_s"], summ["site_updates"] = float(mk[0]), float(t[1])
+    if rank != 0:
+        return
+    value = summ["site_updates"] / summ["makespan_s"] / 1e6
+    res = [r for r in run["results"] if r]
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * summ["makespan_s"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"Poisson request stream, 50/s, seed = rank, {storage}",
+                   "storage": storage, "requests": args.steps, "tol": tol, "max_steps": max_steps,
+                   "check_every": 100, "arena_bytes": arena, "parallelism": f"replicas x{world}"},
+        "serving": {k: summ[k] for k in ("p50_s", "p99_s", "mean_s", "wait_p50_s", "wait_p99_s",
+                                          "status", "makespan_s")},
+        "roofline": None,
+        "e2e": {"value": value, "unit": "MLUPS",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "requests enter and results leave through the host API; the makespan is host wall time"},
+        "gpu_launches": int(run["stats"]["rounds"] * 100),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+WORKLOADS = ["nanotube", "nanotube_large_fp32", "nanotube_large_fp16", "nanotube_large_bf16",
+             "sweep_fp32", "sweep_fp16", "serving_fp32", "serving_fp16"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="nanotube", choices=WORKLOADS)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 48 if args.workload.startswith("serving_") else (
+            4 if args.workload.startswith("sweep_") else 20)
     if args.impl == "reference":
         run_reference(args)
     else:

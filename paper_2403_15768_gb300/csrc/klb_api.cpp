@@ -114,8 +114,9 @@ void fill_args_at(const klb_lattice *L, const HostState &st, int sbx, StepArgs<T
     a.nxp = g.nxp;
     a.nchunk = p.nchunk;
     a.nbw = (int)g.rows[kFluid].size() * a.nchunk;
-    a.snchunk = step_chunks(g.nx, sbx, L->desc.storage);
-    a.snbw = (int)g.rows[kFluid].size() * a.snchunk;
+    a.snchunk_w = step_chunks(g.nx, sbx, L->desc.storage, true);
+    a.snchunk_s = step_chunks(g.nx, sbx, L->desc.storage, false);
+    a.snbw = (int)g.rows[kFluid].size() * a.snchunk_w;
     a.nch32 = (g.nx + 31) / 32;
     a.nseg_w = (int)g.rows[kFluid].size() * a.nch32;
     const klb_desc &d = L->desc;
@@ -888,8 +889,10 @@ klb_status build_tables(klb_batch *B, int width)
             }
             advance(st, sp);
         }
-        const int chunks = step_chunks(L->geo.nx, width, L->desc.storage);
-        prefix[m + 1] = prefix[m] + chunks * (int)(L->geo.rows[kFluid].size() + L->geo.rows[kSolid].size());
+        const int sto = L->desc.storage;
+        prefix[m + 1] = prefix[m] +
+                        step_chunks(L->geo.nx, width, sto, true) * (int)L->geo.rows[kFluid].size() +
+                        step_chunks(L->geo.nx, width, sto, false) * (int)L->geo.rows[kSolid].size();
     }
     KLB_BCUDA(B, cudaStreamSynchronize(B->stream));
     KLB_BCUDA(B, cudaMemcpy(B->base + B->table_off, host.data(), host.size(), cudaMemcpyHostToDevice));

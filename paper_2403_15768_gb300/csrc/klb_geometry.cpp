@@ -313,9 +313,11 @@ MemoryPlan plan_memory(const Geometry &g, int storage)
     p.nblocks_w = (int)nr[kFluid] * p.nchunk;
     p.nblocks_s = (int)nr[kSolid] * p.nchunk;
     {
-        const int xt = (g.nx + step_cells(storage) - 1) / step_cells(storage);  // threads per row
+        const int c = step_cells(storage, false);
+        const int xt = (g.nx + c - 1) / c;  // threads per solid row
         p.sbx = std::min(kBlockX, std::max(32, (xt + 31) / 32 * 32));
-        p.snblocks = (int)(nr[kFluid] + nr[kSolid]) * step_chunks(g.nx, p.sbx, storage);
+        p.snblocks = (int)nr[kFluid] * step_chunks(g.nx, p.sbx, storage, true) +
+                     (int)nr[kSolid] * step_chunks(g.nx, p.sbx, storage, false);
     }
     p.partials = take(sizeof(double) * kNumSums * (size_t)(p.nblocks_w + p.nblocks_s));
     p.sums = take(sizeof(double) * kNumSums);

@@ -104,14 +104,18 @@ constexpr int kRefStride = 20;
 constexpr int kRefEvery = 32;
 constexpr float kFp16Scale = 1048576.0f;  // 2^20
 
-// Cells per thread of the step kernel: two adjacent x with packed FP32
-// arithmetic, one in FP64.
-inline int step_cells(int storage) { return storage == KLB_FP64 ? 1 : 2; }
-
-// Step-kernel blocks of a lattice with nx x-cells, nrows rows, sbx threads.
-inline int step_chunks(int nx, int sbx, int storage)
+// Cells per thread of the step kernel: FP64 one; FP32 arithmetic two
+// adjacent x (packed f32x2).  Per row class, so that the classes may differ.
+inline int step_cells(int storage, bool water)
 {
-    const int xb = sbx * step_cells(storage);
+    (void)water;
+    return storage == KLB_FP64 ? 1 : 2;
+}
+
+// Step-kernel x chunks per row of the given class for blocks of sbx threads.
+inline int step_chunks(int nx, int sbx, int storage, bool water)
+{
+    const int xb = sbx * step_cells(storage, water);
     return (nx + xb - 1) / xb;
 }
 
@@ -132,7 +136,7 @@ struct alignas(16) StepArgs {
     const T *U1[2], *U2[2], *U3[2];  // lagged velocities u(n-1), u(n-2), u(n-3)
     T *U0[2];                        // u(n) written here (step mode)
     int nx, nxp, nchunk, nbw;        // nchunk = x chunks of blockDim.x per row; nbw = water blocks
-    int snchunk, snbw;               // the same for the step kernel (step_cells x per thread)
+    int snchunk_w, snchunk_s, snbw;  // the same for the step kernel, per row class
     int nch32, nseg_w;               // 32-wide x segments per row; water segments
     int n_rows[2], n_slots[2];
     T rho0, om[3], G[3];

@@ -604,10 +604,12 @@ __global__ void __launch_bounds__(kBlockX) k_init(const StepArgs<T> p)
 // ---------------------------------------------------------------------------
 // Step kernel.
 //
-// One block per work item (one row, up to 128 consecutive x), one cell per
-// thread.  Memory parallelism comes from residency: in FP32 the kernel is
-// held to 64 registers (8 blocks of 128 threads per SM), and every thread
-// issues its Q (or 2Q) loads back to back.  The row table is read with
+// One block per work item (one row, up to 128 threads along x).  With FP32
+// arithmetic a thread updates two adjacent cells (klb_step_pair.cuh), in
+// FP64 one (step_body below).  Memory parallelism comes from residency: the
+// FP32-arithmetic kernel is held to 96 registers (5 blocks of 128 threads
+// per SM; a few spilled values cost less than the occupancy they buy), and
+// every thread issues its loads back to back.  The row table is read with
 // 16-byte loads (one 128-byte line per row, cached); the x shift of each
 // direction is a compile-time constant except on the few rows where an
 // x-moving population bounces back.  A solid cell streams, and takes the
@@ -655,7 +657,7 @@ static_assert(offsetof(RowInfo, xm) == 19 * 4 && offsetof(RowInfo, xp) == 20 * 4
 template <typename T, typename S>
 constexpr int step_min_blocks()
 {
-    return sizeof(T) == 8 ? 4 : (Storage<S>::kRef ? 4 : 4);
+    return sizeof(T) == 8 ? 4 : 5;
 }
 
 template <int Q, typename T, typename S, bool ACC>
@@ -663,8 +665,9 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
 {
     const bool water = b < p.snbw;
     const int bb = water ? b : b - p.snbw;
-    const int row = bb / p.snchunk;
-    int x = (bb - row * p.snchunk) * blockDim.x + threadIdx.x;
+    const int nch = water ? p.snchunk_w : p.snchunk_s;
+    const int row = bb / nch;
+    int x = (bb - row * nch) * blockDim.x + threadIdx.x;
     const int x_lane = x;
     const bool live = x < p.nx;
     if constexpr (!ACC) {

@@ -117,15 +117,35 @@ __device__ __forceinline__ float2 cmoment2(int a, const float2 g[Q])
     return r;
 }
 
+// Mass and momentum of a population set, summed through the pairs of
+// opposite directions (s = g_i + g_ibar, d = g_i - g_ibar) in shallow trees,
+// so that the sums are short dependency chains.
 template <int Q>
-__device__ __forceinline__ void moments2(const float2 g[Q], float2 &drho, float2 j[3])
+__device__ __forceinline__ void moments2(const float2 g[Q], float2 &m, float2 j[3])
 {
-    drho = g[0];
+    if constexpr (Q == 19) {
+        // pairs (1,2) x, (3,4) y, (5,6) z, (7,8) +x+y, (9,10) +x-y,
+        // (11,12) +x+z, (13,14) +x-z, (15,16) +y+z, (17,18) +y-z
+        float2 sp[9], d[9];
 #pragma unroll
-    for (int i = 1; i < Q; ++i) drho = add2(drho, g[i]);
-    j[0] = cmoment2<Q>(0, g);
-    j[1] = cmoment2<Q>(1, g);
-    j[2] = Q == 19 ? cmoment2<Q>(2, g) : b2(0.f);
+        for (int k = 0; k < 9; ++k) {
+            sp[k] = add2(g[2 * k + 1], g[2 * k + 2]);
+            d[k] = sub2(g[2 * k + 1], g[2 * k + 2]);
+        }
+        m = add2(add2(add2(add2(sp[0], sp[1]), add2(sp[2], sp[3])), add2(add2(sp[4], sp[5]), add2(sp[6], sp[7]))),
+                 add2(g[0], sp[8]));
+        j[0] = add2(add2(add2(d[0], d[3]), add2(d[4], d[5])), d[6]);
+        j[1] = sub2(add2(add2(d[1], d[3]), add2(d[7], d[8])), d[4]);
+        j[2] = sub2(add2(add2(d[2], d[5]), d[7]), add2(d[6], d[8]));
+    } else {
+        // D2Q9, Sec. 4.2 numbering: pairs (1,3) x, (2,4) y, (5,7) +x+y, (6,8) -x+y
+        const float2 d0 = sub2(g[1], g[3]), d1 = sub2(g[2], g[4]), d2 = sub2(g[5], g[7]), d3 = sub2(g[6], g[8]);
+        m = add2(add2(add2(g[1], g[3]), add2(g[2], g[4])), add2(add2(g[5], g[7]), add2(g[6], g[8])));
+        m = add2(m, g[0]);
+        j[0] = sub2(add2(d0, d2), d3);
+        j[1] = add2(add2(d1, d2), d3);
+        j[2] = b2(0.f);
+    }
 }
 
 // Pull direction i of both cells.  SHIFT is the x shift of the direction's
@@ -251,7 +271,7 @@ __device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const RowI
 
 // BGK + Guo collision of both cells, per pair of opposite directions, then
 // the FP32 fix-up of mass and momentum (see collide).  g is left holding g*.
-template <int Q>
+template <int Q, bool FIX = true>
 __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const float2 j[3], float rho0,
                                          float om)
 {
@@ -282,10 +302,10 @@ __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const floa
         g[i] = fma2(b2(om1), g[i], add2(S, A));
         g[ib] = fma2(b2(om1), g[ib], sub2(S, A));
     }
-    float2 m = g[0];
-#pragma unroll
-    for (int i = 1; i < Q; ++i) m = add2(m, g[i]);
-    const float2 px = cmoment2<Q>(0, g), py = cmoment2<Q>(1, g);
+    if constexpr (!FIX) return;
+    float2 m, pm[3];
+    moments2<Q>(g, m, pm);
+    const float2 px = pm[0], py = pm[1];
     g[0] = add2(g[0], sub2(c.drho, m));
     const float2 hx = mul2(b2(0.5f), sub2(add2(j[0], c.F[0]), px));
     const float2 hy = mul2(b2(0.5f), sub2(add2(j[1], c.F[1]), py));
@@ -294,7 +314,7 @@ __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const floa
     g[dir_index<Q>(0, 1, 0)] = add2(g[dir_index<Q>(0, 1, 0)], hy);
     g[dir_index<Q>(0, -1, 0)] = sub2(g[dir_index<Q>(0, -1, 0)], hy);
     if (Q == 19) {
-        const float2 pz = cmoment2<Q>(2, g);
+        const float2 pz = pm[2];
         const float2 hz = mul2(b2(0.5f), sub2(add2(j[2], c.F[2]), pz));
         g[dir_index<Q>(0, 0, 1)] = add2(g[dir_index<Q>(0, 0, 1)], hz);
         g[dir_index<Q>(0, 0, -1)] = sub2(g[dir_index<Q>(0, 0, -1)], hz);
@@ -329,21 +349,33 @@ __device__ __forceinline__ void store_u2(float *q, float2 v, bool both)
         *q = v.x;
 }
 
-// x-sums over the 32-wide segment of a half warp (16 threads, 32 cells) of
-// NV pair values, written by lanes 0 and 16.
-template <int NV>
-__device__ __forceinline__ void halfwarp_xsum(const float2 (&v)[NV], float *out_lo, float *out_hi,
-                                              bool lo_ok, bool hi_ok)
+// x-sums over the 32-wide segments of a warp whose threads hold CPT cells
+// each (32 / CPT threads per segment) of NV per-thread values (the sums of
+// their live cells), written by the first thread of each segment to
+// acc + seg * 2Q; a segment past the end of the row (seg < 0) is skipped.
+template <int CPT, int NV>
+__device__ __forceinline__ void segment_xsum(const float (&v)[NV], float *acc, int seg, int stride)
 {
+    constexpr int L = 32 / CPT;
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        float s = v[k].x + v[k].y;
+        float s = v[k];
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0 && lo_ok) out_lo[k] = s;
-        if (lane == 16 && hi_ok) out_hi[k] = s;
+        for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((lane & (L - 1)) == 0 && seg >= 0) acc[(size_t)seg * stride + k] = s;
     }
+}
+
+// Segment of the calling thread's cells: the warp's first x plus 32 per
+// segment, or -1 past the end of the row.
+template <int CPT>
+__device__ __forceinline__ int thread_segment(const StepArgs<float> &p, bool water, int row, int x_first)
+{
+    const int lane = threadIdx.x & 31;
+    const int xs = x_first - CPT * lane + 32 * (lane / (32 / CPT));  // first x of the segment
+    if (xs >= p.nx) return -1;
+    return (water ? 0 : p.nseg_w) + row * p.nch32 + xs / 32;
 }
 
 template <int Q, typename S, bool ACC>
@@ -351,8 +383,9 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
 {
     const bool water = b < p.snbw;
     const int bb = water ? b : b - p.snbw;
-    const int row = bb / p.snchunk;
-    const int xt = (bb - row * p.snchunk) * blockDim.x + threadIdx.x;
+    const int nch = water ? p.snchunk_w : p.snchunk_s;
+    const int row = bb / nch;
+    const int xt = (bb - row * nch) * blockDim.x + threadIdx.x;
     const int x_first = 2 * xt;
     const bool live = x_first < p.nx;
     if constexpr (!ACC) {
@@ -384,15 +417,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     const uint32_t xp = (uint32_t)q5.x;
     const bool xbounce = (q7.x & kXBounce) != 0;
 
-    // ACC segments: half warp h of this warp covers x from seg_x0 + 32 h.
-    int seg_lo = -1, seg_hi = -1;
-    if constexpr (ACC) {
-        const int lane = threadIdx.x & 31;
-        const int xw = x_first - 2 * lane;  // first x of the warp
-        const int base = (water ? 0 : p.nseg_w) + row * p.nch32 + xw / 32;
-        if (xw < p.nx) seg_lo = base;
-        if (xw + 32 < p.nx) seg_hi = base + 1;
-    }
+    const int seg = ACC ? thread_segment<2>(p, water, row, x_first) : -1;
 
     if (water) {
         float2 g[Q], j[3];
@@ -409,14 +434,13 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
             store_pair<Q, S>(g, static_cast<S *>(p.out[0]), p.n_rows[kFluid] * nxp, row * nxp + X.x0, both,
                              ref_row<float, S>(p.enc_out[0], row), sc);
         if constexpr (ACC) {
-            float2 acc[2 * Q];
+            float acc[2 * Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                acc[i] = make_float2(live ? g[i].x : 0.f, both ? g[i].y : 0.f);
-                acc[Q + i] = b2(0.f);
+                acc[i] = (live ? g[i].x : 0.f) + (both ? g[i].y : 0.f);
+                acc[Q + i] = 0.f;
             }
-            halfwarp_xsum<2 * Q>(acc, p.acc + (size_t)seg_lo * 2 * Q, p.acc + (size_t)seg_hi * 2 * Q,
-                                 seg_lo >= 0, seg_hi >= 0);
+            segment_xsum<2, 2 * Q>(acc, p.acc, seg, 2 * Q);
         }
         return;
     }
@@ -440,10 +464,10 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     if (live)
         store_pair<Q, S>(ge, static_cast<S *>(p.out[1]), stride, base, both,
                          ref_row<float, S>(p.enc_out[1], row), sc);
-    float2 acc[ACC ? 2 * Q : 1];
+    float acc[ACC ? 2 * Q : 1];
     if constexpr (ACC) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) acc[i] = make_float2(live ? ge[i].x : 0.f, both ? ge[i].y : 0.f);
+        for (int i = 0; i < Q; ++i) acc[i] = (live ? ge[i].x : 0.f) + (both ? ge[i].y : 0.f);
     }
     pull_row2<Q, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, X,
                     ref_row<float, S>(p.dec_in[2], row), inv, gp);
@@ -453,9 +477,8 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
                          ref_row<float, S>(p.enc_out[2], row), sc);
     if constexpr (ACC) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) acc[Q + i] = make_float2(live ? gp[i].x : 0.f, both ? gp[i].y : 0.f);
-        halfwarp_xsum<2 * Q>(acc, p.acc + (size_t)seg_lo * 2 * Q, p.acc + (size_t)seg_hi * 2 * Q,
-                             seg_lo >= 0, seg_hi >= 0);
+        for (int i = 0; i < Q; ++i) acc[Q + i] = (live ? gp[i].x : 0.f) + (both ? gp[i].y : 0.f);
+        segment_xsum<2, 2 * Q>(acc, p.acc, seg, 2 * Q);
     }
 }
 

@@ -84,12 +84,15 @@ def test_admission_waits_for_arena_space():
 
 
 def test_step_limit_and_unstable_requests():
+    """A drive of 1e30 overflows FP32 velocities in the first step; the
+    request is retired as unstable at its first check."""
     w = STREAM[0].w
-    blow = w.with_(G=(0.3, 0.0, 0.0), tau=(0.501, 0.6, 1.0), couplings=(0.0,) * 5)
+    blow = w.with_(G=(1e30, 0.0, 0.0))
     reqs = [inputs.Request(0, 0.0, w), inputs.Request(1, 0.0, blow)]
     out, _ = _run(reqs, 4 * (_bytes(w) + 2 ** 26), check_every=64, tol=1e-30, max_steps=100)
     assert out[0]["status"] == 5 and out[0]["steps"] == 128  # KLB_ETIMEOUT at the first check >= 100
     assert out[1]["status"] == 4 and out[1]["obs"]["nonfinite"] > 0  # KLB_EUNSTABLE
+    assert out[1]["steps"] == 64
 
 
 def test_replay_reports_latencies():
