@@ -26,7 +26,8 @@
  *      trapezoidal in time, solved exactly per cell; water velocity with the
  *      pressure drive of Eq. 2 as a uniform body force;
  *   5. U2 := U, U := u for the next step;
- *   6. BGK collision with Guo forcing.
+ *   6. BGK collision with Guo forcing;
+ *   7. optionally, thermal fluctuations of the water (see thermal_noise()).
  */
 #include <math.h>
 #include <stdint.h>
@@ -66,6 +67,8 @@ typedef struct {
     double *u[3];    /* velocity of the current step, [a*ncell + cell] */
     double *F[3];    /* total force density of the current step        */
     long step;
+    double kT;       /* thermal energy of the water fluctuations (0: off) */
+    uint32_t key[2]; /* generator key (seed)                              */
 } kor_t;
 
 /* ------------------------------------------------------------------ */
@@ -319,6 +322,110 @@ void kor_set_couplings(kor_t *o, double g_we, double g_wp, double g_ep, double g
     o->g_pc = g_pc;
 }
 
+/* ------------------------------------------------------------------ */
+/* Thermal fluctuations (Eq. 6: the classical fluctuation-dissipation
+ * relation of the fluctuating momentum flux; Eq. 17: its lattice source, a
+ * random stress projected on w_i (c_ia c_ib - cs^2 delta_ab)), read as the
+ * standard fluctuating lattice Boltzmann method: every non-conserved moment
+ * of the post-collision water populations receives Gaussian noise of the
+ * variance that the relaxation removes, so that each mode m_k keeps
+ * <m_k^2> = mu b_k with mu = rho0 kT / cs^2.  With one relaxation rate for
+ * all non-conserved moments (BGK) this is weighted Gaussian noise with its
+ * mass and momentum projected out:
+ *   a_i = sqrt(w_i) z_i,  z_i ~ N(0, 1) independent,
+ *   xi_i = A (a_i - w_i sum_j a_j - 3 w_i c_i . sum_j c_j a_j),
+ *   A = sqrt(mu (1 - (1 - omega)^2)) = sqrt(3 rho0 kT omega (2 - omega)),
+ * whose stress part is the source of Eq. 17.  Electrons and phonons are not
+ * thermalised.
+ *
+ * Random numbers: the Philox-4x32-10 counter-based generator of Salmon,
+ * Moraes, Dror and Shaw (SC 2011), from its definition: ten rounds, each
+ * multiplying counter words 0 and 2 by M0 and M1 into 64-bit products and
+ * recombining (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), the key bumped by the
+ * Weyl constants W0, W1 between rounds.  Counter (cell, step mod 2^32,
+ * step / 2^32, k) for k = 0, 1, ...; key = the 64-bit seed.  Each output
+ * word r gives u = (r + 1/2) 2^-32, and pairs (u1, u2) give two normals by
+ * Box-Muller: sqrt(-2 ln u1) (cos, sin)(2 pi u2).                         */
+
+static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+    memcpy(out, c, sizeof c);
+}
+
+/* Q standard normals of one cell and step. */
+static void cell_normals(const kor_t *o, long cell, long step, double *z)
+{
+    const double two32 = 4294967296.0;
+    const double pi = 3.14159265358979323846;
+    int n = 0;
+    for (uint32_t k = 0; n < o->Q; k++) {
+        uint32_t ctr[4] = {(uint32_t)cell, (uint32_t)((uint64_t)step & 0xffffffffu),
+                           (uint32_t)((uint64_t)step >> 32), k};
+        uint32_t r[4];
+        philox4x32_10(ctr, o->key, r);
+        for (int h = 0; h < 4 && n < o->Q; h += 2) {
+            double u1 = ((double)r[h] + 0.5) / two32, u2 = ((double)r[h + 1] + 0.5) / two32;
+            double R = sqrt(-2.0 * log(u1));
+            z[n++] = R * cos(2.0 * pi * u2);
+            if (n < o->Q) z[n++] = R * sin(2.0 * pi * u2);
+        }
+    }
+}
+
+/* Test hook: the four Philox-4x32-10 output words for a counter and key. */
+void kor_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) { philox4x32_10(ctr, key, out); }
+
+/* 7. Thermal noise on the post-collision water populations (see above). */
+static void thermal_noise(kor_t *o)
+{
+    const long N = o->ncell;
+    const double om = 1.0 / o->tau[SW];
+    const double A = sqrt(3.0 * o->rho0 * o->kT * om * (2.0 - om));
+    for (int z = 0; z < o->nz; z++)
+        for (int y = 0; y < o->ny; y++)
+            for (int x = 0; x < o->nx; x++) {
+                int X[3] = {x, y, z};
+                if (!carries(o, SW, X)) continue;
+                long k = cell_index(o, X);
+                double zz[19], a[19], S0 = 0.0, S1[3] = {0.0, 0.0, 0.0};
+                cell_normals(o, k, o->step, zz);
+                for (int i = 0; i < o->Q; i++) {
+                    a[i] = sqrt(o->w[i]) * zz[i];
+                    S0 += a[i];
+                    for (int d = 0; d < 3; d++) S1[d] += o->c[i][d] * a[i];
+                }
+                for (int i = 0; i < o->Q; i++) {
+                    const int *c = o->c[i];
+                    double cS = c[0] * S1[0] + c[1] * S1[1] + c[2] * S1[2];
+                    o->gs[SW][i * N + k] += A * (a[i] - o->w[i] * S0 - 3.0 * o->w[i] * cS);
+                }
+            }
+}
+
+void kor_set_fluctuations(kor_t *o, double kT, uint64_t seed)
+{
+    o->kT = kT;
+    o->key[0] = (uint32_t)(seed & 0xffffffffu);
+    o->key[1] = (uint32_t)(seed >> 32);
+}
+
 /* Second-order polynomial equilibrium in deviation form (Sec. 4: second-order
  * expansion of the local equilibrium in the flow field), rho = rho0 + drho. */
 static double geq(const kor_t *o, int i, double drho, const double u[3])
@@ -523,6 +630,7 @@ void kor_step(kor_t *o, long nsteps)
             memcpy(o->U[s], o->u[s], sizeof(double) * 3 * o->ncell);
         }
         collide(o);
+        if (o->kT > 0.0) thermal_noise(o);
         o->step++;
     }
 }

@@ -68,6 +68,8 @@ def _load():
     lib.kor_destroy.argtypes = [P]
     lib.kor_set_params.argtypes = [P, D, D, D, D, D, D, D, I]
     lib.kor_set_couplings.argtypes = [P, D, D, D, D, D]
+    lib.kor_set_fluctuations.argtypes = [P, D, ctypes.c_uint64]
+    lib.kor_philox.argtypes = [P, P, P]
     lib.kor_init_equilibrium.argtypes = [P, P, P]
     lib.kor_step.argtypes = [P, L]
     lib.kor_observe.argtypes = [P, P, P, P, P]
@@ -191,6 +193,10 @@ class Oracle:
     # shapes
     def _box(self, *lead):
         return (*lead, self.nz, self.ny, self.nx)
+
+    def set_fluctuations(self, kT: float, seed: int):
+        """Thermal noise of the water populations (0 disables)."""
+        _lib.kor_set_fluctuations(self._h, float(kT), int(seed))
 
     def set_couplings(self, g_we, g_wp, g_ep, g_ec=0.0, g_pc=0.0):
         self.couplings = (g_we, g_wp, g_ep, g_ec, g_pc)
@@ -360,3 +366,13 @@ def slip_poiseuille_pipe(G, rho, tau, R, Ls):
     prof = lambda r: G / (4 * rho * nu) * (R * R - np.asarray(r) ** 2) + us  # noqa: E731
     Q = np.pi * G * R ** 4 / (8 * rho * nu) * (1 + 4 * Ls / R)
     return prof, Q
+
+
+def philox4x32_10(ctr, key):
+    """The oracle's Philox-4x32-10 words for a counter (4 words) and key (2)."""
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    _load().kor_philox(c.ctypes.data_as(ctypes.c_void_p), k.ctypes.data_as(ctypes.c_void_p),
+                    out.ctypes.data_as(ctypes.c_void_p))
+    return out

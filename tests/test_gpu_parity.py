@@ -280,3 +280,35 @@ def test_coupling_validation_and_buffer_size():
     st = klb.load_library().klb_create_lattice(ctypes.byref(d), ctypes.c_void_p(buf.data_ptr()),
                                                n - 256, None, ctypes.byref(h))
     assert st == 2 and not h.value
+
+
+def test_negative_friction_against_oracle():
+    """Negative water-electron friction (Sec. 2) inside the stability bound:
+    FP64 and FP32 lattices follow the oracle from a perturbed start."""
+    for storage, tol in (("fp64", 1e-11), ("fp32", 2e-4)):
+        w = SMALL_PIPE.with_(nx=40, storage=storage, couplings=(-0.03, 0.05, 0.1, 0.0, 0.01))
+        o, lat = _pair(w, seed=4, eps=1e-3)
+        o.step(300)
+        lat.step(300)
+        _compare_fields(o, lat, tol, w)
+
+
+def test_checkpoint_resume_is_bitwise():
+    """A state read with klb_get_state and loaded into a fresh lattice with
+    klb_set_state continues exactly as the original (FP32 and FP64 states
+    round-trip through the FP64 host arrays without loss)."""
+    for storage in ("fp32", "fp64"):
+        w = SMALL_PIPE.with_(nx=50, storage=storage)
+        a = klb.lattice_from_workload(w)
+        d, u = inputs.perturbation(w, 5, 1e-3)
+        a.init_equilibrium(d, u)
+        a.step(57)
+        g, U1, U2 = a.get_state()
+        b = klb.lattice_from_workload(w)
+        b.set_state(g, U1, U2, step=57)
+        assert b.nstep == 57
+        a.step(43)
+        b.step(43)
+        for x, y in zip(a.get_state(), b.get_state()):
+            assert np.array_equal(x, y)
+        assert a.observables()["flow_rate"] == b.observables()["flow_rate"]

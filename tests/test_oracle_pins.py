@@ -610,3 +610,106 @@ def test_pipe_eightfold_symmetry():
             assert np.abs(ux - img).max() < 1e-12 * scale
         uy, uz = f["u"][s, 1][:, :, 0], f["u"][s, 2][:, :, 0]
         assert np.abs(uy - uz.T).max() < 1e-12 * scale
+
+
+# ---------------------------------------------------------------------------
+# Negative quantum friction (Sec. 2: the couplings may "go both ways"):
+# a negative water-electron coupling inside the stability bound.
+
+NEG = dict(tau=(0.8, 0.6, 1.0), G=(1e-6, 0, 0), couplings=(-0.02, 0.05, 0.1, 0.0, 0.01))
+
+
+def test_negative_friction_steady_slab():
+    """With g_we < 0 the steady slab still balances the drive at each wall
+    (P7: G H/2 = g_we (u_w - u_e) + g_wp (u_w - u_p), here with one term of
+    each sign), and equals the independent dense steady solve (P8)."""
+    rows = [T_SOLID] * 4 + [T_FLUID] * 32 + [T_SOLID] * 4
+    o, geo = _slab(**NEG)
+    o.init_equilibrium()
+    u = _run_to_steady(o)
+    uw, ue, up = u[0, 0, 0, :, 0], u[1, 0, 0, :, 0], u[2, 0, 0, :, 0]
+    G, H = 1e-6, 32
+    bottom = -0.02 * (uw[4] - ue[3]) + 0.05 * (uw[4] - up[3])
+    assert abs(bottom - G * H / 2) < 1e-12 * G * H
+    assert -0.02 * (uw[4] - ue[3]) < 0  # the electron term pushes the water
+    ref = _independent_steady_slab(NEG["tau"], 1e-6, NEG["couplings"], rows)
+    for s in range(3):
+        m = ref[s] != 0
+        assert np.abs(u[s, 0, 0, :, 0][m] - ref[s][m]).max() < 1e-10 * np.abs(ref[0]).max()
+
+
+# ---------------------------------------------------------------------------
+# Thermal fluctuations (Eq. 6, Eq. 17): the generator, exact conservation,
+# and equipartition of the fluctuating lattice fluid.
+
+def test_philox_generator_statistics():
+    """Philox-4x32-10 words are uniform, uncorrelated between neighbouring
+    counters and words, distinct over a sample of counters (the map is a
+    bijection of the counter), and change about half their bits when one key
+    bit flips."""
+    from oracle.oracle import philox4x32_10
+
+    n = 4096
+    out = np.array([philox4x32_10([c, 7, 0, k], [0x1234, 0x9abc]) for c in range(n // 4) for k in range(4)],
+                   np.uint64).ravel()
+    u = (out.astype(np.float64) + 0.5) / 2.0 ** 32
+    assert abs(u.mean() - 0.5) < 4 * math.sqrt(1 / 12 / u.size)
+    assert abs(u.var() - 1 / 12) < 0.05 / 12
+    hist, _ = np.histogram(u, bins=64, range=(0, 1))
+    chi2 = ((hist - u.size / 64) ** 2 / (u.size / 64)).sum()
+    assert chi2 < 63 + 5 * math.sqrt(2 * 63)
+    assert abs(np.corrcoef(u[:-1], u[1:])[0, 1]) < 4 / math.sqrt(u.size)
+    assert len(np.unique(out)) == out.size
+    a = np.array([philox4x32_10([c, 0, 0, 0], [1, 2]) for c in range(256)], np.uint32)
+    b = np.array([philox4x32_10([c, 0, 0, 0], [1 ^ 8, 2]) for c in range(256)], np.uint32)
+    flips = np.unpackbits((a ^ b).view(np.uint8)).mean()
+    assert abs(flips - 0.5) < 0.03
+
+
+def test_thermal_noise_conserves_mass_and_momentum():
+    """The noise is projected off mass and momentum: with no drive and no
+    coupling the water's total mass and x-momentum stay at zero to rounding
+    while the populations fluctuate."""
+    geo = cross_section("slab", 24, 1, width=16, shell=4)
+    o = Oracle(9, 16, geo, tau=(0.8, 0.6, 1.0), G=(0, 0, 0), couplings=(0, 0, 0, 0, 0))
+    o.init_equilibrium()
+    o.set_fluctuations(1e-5, 99)
+    o.step(50)
+    f = o.observe()
+    fluid = np.broadcast_to((geo.cs_type == 1)[..., None], f["drho"][0].shape)
+    d = f["drho"][0][fluid]
+    jx = ((1.0 + f["drho"][0]) * f["u"][0][0])[fluid]
+    assert np.abs(d).max() > 1e-4  # fluctuating
+    assert abs(d.sum()) < 1e-12 and abs(jx.sum()) < 1e-12
+
+
+@pytest.mark.parametrize("Q,tau", [(9, 0.8), (9, 1.0), (19, 0.8)])
+def test_equipartition(Q, tau):
+    """Fluctuation-dissipation of the lattice fluid: at rest with thermal
+    noise every velocity component of a fluid cell has rho0 <u_a^2> = kT and
+    the density <drho^2> = rho0 kT / cs^2 (slab with specular walls, isolated
+    water).  Tolerance: 3% (several thousand effectively independent
+    samples)."""
+    nz = 1 if Q == 9 else 4
+    geo = cross_section("slab", 24, nz, width=16, shell=4)
+    o = Oracle(Q, 32, geo, tau=(tau, 0.6, 1.0), G=(0, 0, 0), couplings=(0, 0, 0, 0, 0))
+    o.init_equilibrium()
+    kT = 1e-5
+    o.set_fluctuations(kT, 2024)
+    o.step(500)
+    fluid = geo.cs_type == 1
+    acc, n = np.zeros(4), 0
+    for _ in range(200 if Q == 9 else 60):
+        o.step(5)
+        f = o.observe()
+        m = np.broadcast_to(fluid[..., None], f["drho"][0].shape)
+        u = f["u"][0]
+        acc += [np.mean(u[0][m] ** 2), np.mean(u[1][m] ** 2), np.mean(u[2][m] ** 2),
+                np.mean(f["drho"][0][m] ** 2)]
+        n += 1
+    acc /= n
+    assert acc[0] == pytest.approx(kT, rel=0.03)
+    assert acc[1] == pytest.approx(kT, rel=0.03)
+    if Q == 19:
+        assert acc[2] == pytest.approx(kT, rel=0.03)
+    assert acc[3] == pytest.approx(3 * kT, rel=0.03)
