@@ -186,9 +186,26 @@ klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
 /* Set the friction coefficients.  KLB_EINVAL for non-finite values or for
  * couplings beyond the stability bound of the lagged interface exchange:
  * max over cells of (sum over its faces of |g| of its species pairs) must be
- * below 0.6 rho0 (the exchange is stable for a pair relaxation rate below
- * 4/3; see the design notes).  Host only; takes effect at the next step. */
+ * below 0.6 rho0 (the two-step-averaged exchange of one face pair is stable
+ * for kappa = g (1/rho_k + 1/rho_l) < 4/3, with a margin for density
+ * deviations).  Host only; takes effect at the next step. */
 klb_status klb_set_couplings(klb_lattice *lat, const klb_couplings *c);
+
+/* Thermal fluctuations of the water (Eq. 6, the classical
+ * fluctuation-dissipation relation of the momentum flux; Eq. 17, its
+ * lattice source), in the standard fluctuating lattice Boltzmann form:
+ * after each collision the water populations of every fluid cell receive
+ *   xi_i = A (a_i - w_i sum_j a_j - 3 w_i c_i . sum_j c_j a_j),
+ *   a_i = sqrt(w_i) z_i,  A = sqrt(3 rho0 kT omega_w (2 - omega_w)),
+ * with z_i standard normals (Box-Muller) from the Philox-4x32-10
+ * counter-based generator keyed by `seed`, counter (x + nx (y + ny z),
+ * step mod 2^32, step / 2^32, block of four words).  The noise carries no
+ * mass or momentum; the lattice fluid then holds rho0 <u_a^2> = kT.
+ * Electrons and phonons are not thermalised.  kT = 0 switches the noise
+ * off.  KLB_EINVAL for a negative or non-finite kT, or kT > 0 with 16-bit
+ * storage.  Host only; takes effect at the next step.  A lattice with noise
+ * cannot join a batch. */
+klb_status klb_set_fluctuations(klb_lattice *lat, double kT, uint64_t seed);
 
 /* Start from the local equilibrium of host fields in box layout:
  * drho[3][ncell] density deviations and u[3][3][ncell] velocities (either

@@ -38,6 +38,8 @@ struct klb_lattice {
     cudaStream_t stream = nullptr;
     char *base = nullptr;
     klb_couplings cp{0, 0, 0, 0, 0};
+    double kT = 0.0;          // thermal fluctuations of the water (0: off)
+    uint64_t seed = 0;
     HostState st;
     std::string err;
 };
@@ -133,6 +135,12 @@ void fill_args_at(const klb_lattice *L, const HostState &st, int sbx, StepArgs<T
     a.partials = (double *)dev(L, p.partials);
     a.residual_valid = st.since_reset >= 2;
     a.field = (T *)dev(L, p.field);
+    const double om = 1.0 / d.tau_w;
+    a.noise_amp = (T)(L->kT > 0.0 ? std::sqrt(3.0 * d.rho0 * L->kT * om * (2.0 - om)) : 0.0);
+    a.key[0] = (uint32_t)(L->seed & 0xffffffffu);
+    a.key[1] = (uint32_t)(L->seed >> 32);
+    a.step_lo = (uint32_t)((uint64_t)n & 0xffffffffu);
+    a.step_hi = (uint32_t)((uint64_t)n >> 32);
 }
 
 template <typename T>
@@ -412,6 +420,17 @@ klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
     return KLB_OK;
 }
 
+klb_status klb_set_fluctuations(klb_lattice *L, double kT, uint64_t seed)
+{
+    if (!L) return fail(L, KLB_EINVAL, "null handle");
+    if (!(kT >= 0.0) || !std::isfinite(kT)) return fail(L, KLB_EINVAL, "kT must be finite and >= 0");
+    if (kT > 0.0 && reduced(L))
+        return fail(L, KLB_EINVAL, "thermal fluctuations need FP32 or FP64 storage");
+    L->kT = kT;
+    L->seed = seed;
+    return KLB_OK;
+}
+
 klb_status klb_set_couplings(klb_lattice *L, const klb_couplings *c)
 {
     if (!L || !c) return fail(L, KLB_EINVAL, "null argument");
@@ -452,8 +471,8 @@ klb_status klb_step(klb_lattice *L, int64_t nsteps)
         }
         cudaError_t e = with_args(L, [&](void *a) {
             set_enc(L, a, sp.outgen);
-            return launch(L->geo.Q, L->desc.storage, a, sp.acc ? kModeStepAcc : kModeStep,
-                          L->plan.snblocks, L->plan.sbx, L->stream);
+            const int mode = sp.acc ? kModeStepAcc : (L->kT > 0.0 ? kModeStepNoise : kModeStep);
+            return launch(L->geo.Q, L->desc.storage, a, mode, L->plan.snblocks, L->plan.sbx, L->stream);
         });
         if (e != cudaSuccess) return cuda_fail(L, e, "step kernel launch");
         advance(L->st, sp);
@@ -1042,6 +1061,8 @@ klb_status klb_batch_create(klb_lattice *const *members, int n, void *dev_buf, s
             return fail(nullptr, KLB_EINVAL, "batch members must share one CUDA stream");
         for (int k = 0; k < m; ++k)
             if (members[k] == L) return fail(nullptr, KLB_EINVAL, "a lattice appears twice in the batch");
+        if (L->kT > 0.0)
+            return fail(nullptr, KLB_EINVAL, "lattices with thermal fluctuations cannot be batched");
     }
     klb_batch *B = new (std::nothrow) klb_batch();
     if (!B) return fail(nullptr, KLB_ENOMEM, "host allocation failed");

@@ -185,6 +185,7 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
             std::memset(&ri, 0, sizeof ri);
             ri.slot = -1;
             int k = g.rows[cls][r], y = k % d.ny, z = k / d.ny;
+            ri.cs = k;
             for (int f = 0; f < nfaces_dirs; ++f) {
                 int yy = y + face_dir[f][0], zz = z + face_dir[f][1];
                 if (cs.type(yy, zz) == class_cell_type(other)) {

@@ -31,7 +31,8 @@ struct RowInfo {
     float d2;                   // fluid rows: squared distance to centre plane / axis
     int32_t flags;              // bit 0 in the slip fit, bit 1 wall row (fluid rows);
                                 // bit 2: some direction with c_x != 0 bounces back
-    int32_t pad[3];
+    int32_t cs;                 // cross-section cell y + ny z (cell x + nx cs of the box)
+    int32_t pad[2];
 };
 static_assert(sizeof(RowInfo) == 128, "RowInfo is one 128-byte line");
 
@@ -149,6 +150,10 @@ struct alignas(16) StepArgs {
     const float *enc_out[3];               // references of stored populations
     float scale, inv_scale;
     float *acc;            // x-sums of g* per 32-wide segment [segment][2Q]
+    // thermal fluctuations of the water (step with noise only)
+    T noise_amp;           // sqrt(3 rho0 kT omega (2 - omega))
+    uint32_t key[2];       // generator key (seed)
+    uint32_t step_lo, step_hi;  // the step being taken
 };
 
 enum Mode {
@@ -157,7 +162,8 @@ enum Mode {
     kModeField = 2,
     kModeStepAcc = 3,  // step that also writes the x-sums for a refresh
     kModeInit = 4,
-    kModeInitAcc = 5   // x-sums of the initial equilibria, nothing stored
+    kModeInitAcc = 5,  // x-sums of the initial equilibria, nothing stored
+    kModeStepNoise = 6 // step with thermal fluctuations of the water
 };
 
 // Launchers (return the launch error, if any).

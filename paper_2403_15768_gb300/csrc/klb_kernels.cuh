@@ -651,8 +651,109 @@ __device__ __forceinline__ void pull_row(const S *__restrict__ in, const int src
 
 // The kernel reads the row record as eight 16-byte words.
 static_assert(offsetof(RowInfo, xm) == 19 * 4 && offsetof(RowInfo, xp) == 20 * 4 &&
-                  offsetof(RowInfo, slot) == 21 * 4 && offsetof(RowInfo, flags) == 28 * 4,
+                  offsetof(RowInfo, slot) == 21 * 4 && offsetof(RowInfo, flags) == 28 * 4 &&
+                  offsetof(RowInfo, cs) == 29 * 4,
               "row record layout");
+
+// ---------------------------------------------------------------------------
+// Thermal fluctuations of the water (Eq. 6, Eq. 17), read as the standard
+// fluctuating lattice Boltzmann method: after the collision every
+// non-conserved moment of the water populations gets the Gaussian noise its
+// relaxation removes, i.e. g*_i += A (a_i - w_i sum_j a_j - 3 w_i c_i . sum_j
+// c_j a_j) with a_i = sqrt(w_i) z_i, z_i independent standard normals and
+// A = sqrt(3 rho0 kT omega (2 - omega)).  The normals of cell (x, cs) at step
+// n come from the Philox-4x32-10 counter-based generator (Salmon et al.,
+// SC 2011: ten rounds of two 32x32->64-bit products recombined as
+// (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), the key bumped by the Weyl
+// constants between rounds) with counter (x + nx cs, n mod 2^32, n / 2^32,
+// block) and the seed as key; each word r gives u = (r + 1/2) 2^-32 and
+// pairs of uniforms give two normals by Box-Muller.
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Two normals from two generator words (Box-Muller).  FP32: u = r 2^-32 +
+// 2^-33 (exact for small r, where the logarithm is sensitive).
+__device__ __forceinline__ void box_muller(uint32_t r1, uint32_t r2, float &z1, float &z2)
+{
+    const float u1 = fmaf(__uint2float_rn(r1), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float u2 = fmaf(__uint2float_rn(r2), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float R = sqrtf(-2.f * logf(u1));
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    z1 = R * cs;
+    z2 = R * sn;
+}
+__device__ __forceinline__ void box_muller(uint32_t r1, uint32_t r2, double &z1, double &z2)
+{
+    const double u1 = ((double)r1 + 0.5) * 2.3283064365386963e-10;
+    const double u2 = ((double)r2 + 0.5) * 2.3283064365386963e-10;
+    const double R = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    z1 = R * cs;
+    z2 = R * sn;
+}
+
+// sqrt(w_i) (textbook weights 1/3, 1/18, 1/36 and 4/9, 1/9, 1/36).
+template <int Q>
+__host__ __device__ constexpr double sqrt_wt(int i)
+{
+    return Q == 19 ? (i == 0 ? 0.57735026918962576451 : (i <= 6 ? 0.23570226039551584147 : 1.0 / 6.0))
+                   : (i == 0 ? 2.0 / 3.0 : (i <= 4 ? 1.0 / 3.0 : 1.0 / 6.0));
+}
+
+// Calls f(i, a_i) for the Q weighted normals a_i = sqrt(w_i) z_i of a cell.
+template <int Q, typename T, typename F>
+__device__ __forceinline__ void weighted_normals(uint32_t cell, uint32_t slo, uint32_t shi, uint32_t k0,
+                                                 uint32_t k1, F f)
+{
+#pragma unroll
+    for (int b = 0; b < (Q + 3) / 4; ++b) {
+        const uint4 r = philox4x32_10(make_uint4(cell, slo, shi, (uint32_t)b), k0, k1);
+        T z[4];
+        box_muller(r.x, r.y, z[0], z[1]);
+        box_muller(r.z, r.w, z[2], z[3]);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int i = 4 * b + h;
+            if (i < Q) f(i, T(sqrt_wt<Q>(i)) * z[h]);
+        }
+    }
+}
+
+// Calls add(i, xi_i) with the noise of one water cell (see above); the
+// normals are drawn twice (sums, then terms) rather than held.
+template <int Q, typename T, typename F>
+__device__ __forceinline__ void thermal_noise(const StepArgs<T> &p, uint32_t cell, F add)
+{
+    T S0 = T(0), S1[3] = {T(0), T(0), T(0)};
+    weighted_normals<Q, T>(cell, p.step_lo, p.step_hi, p.key[0], p.key[1], [&](int i, T a) {
+        S0 += a;
+        if (cx<Q>(i)) S1[0] += T(cx<Q>(i)) * a;
+        if (cy<Q>(i)) S1[1] += T(cy<Q>(i)) * a;
+        if (cz<Q>(i)) S1[2] += T(cz<Q>(i)) * a;
+    });
+    const T A = p.noise_amp;
+    weighted_normals<Q, T>(cell, p.step_lo, p.step_hi, p.key[0], p.key[1], [&](int i, T a) {
+        const T w = T(wt<Q>(i));
+        const T cS = T(cx<Q>(i)) * S1[0] + T(cy<Q>(i)) * S1[1] + T(cz<Q>(i)) * S1[2];
+        add(i, A * (a - w * S0 - T(3) * w * cS));
+    });
+}
 
 template <typename T, typename S>
 constexpr int step_min_blocks()
@@ -660,7 +761,7 @@ constexpr int step_min_blocks()
     return sizeof(T) == 8 ? 4 : 5;
 }
 
-template <int Q, typename T, typename S, bool ACC>
+template <int Q, typename T, typename S, bool ACC, bool NOISE = false>
 __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
 {
     const bool water = b < p.snbw;
@@ -693,7 +794,7 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
     }
     const uint32_t xm = (uint32_t)src[19];  // the 20th word of a row is its xm mask
     const int4 q5 = __ldg(t4 + 5);          // xp, slot, nface, partner[0]
-    const int4 q7 = __ldg(t4 + 7);          // flags, pad, pad, pad
+    const int4 q7 = __ldg(t4 + 7);          // flags, cs, pad, pad
     const uint32_t xp = (uint32_t)q5.x;
     const bool xbounce = (q7.x & kXBounce) != 0;
 
@@ -709,6 +810,9 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
                 for (int a = 0; a < 3; ++a) p.U0[kFluid][(a * ns + q5.y) * nxp + x] = c.u[a];
             }
             collide<Q, T>(g, c, j, p.rho0, p.om[0]);
+            if constexpr (NOISE)
+                thermal_noise<Q, T>(p, (uint32_t)x + (uint32_t)p.nx * (uint32_t)q7.y,
+                                    [&](int i, T v) { g[i] += v; });
             store_cell<Q, T, S>(g, static_cast<S *>(p.out[0]), p.n_rows[kFluid] * nxp,
                                 row * nxp + x, ref_row<T, S>(p.enc_out[0], row), sc);
         }
@@ -776,19 +880,19 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
 namespace klb {
 
 // FP32 arithmetic: two cells per thread (klb_step_pair.cuh); FP64: one.
-template <int Q, typename T, typename S, bool ACC>
+template <int Q, typename T, typename S, bool ACC, bool NOISE = false>
 __device__ __forceinline__ void step_cells_body(const StepArgs<T> &p, int b)
 {
     if constexpr (sizeof(T) == 4)
-        step_body2<Q, S, ACC>(p, b);
+        step_body2<Q, S, ACC, NOISE>(p, b);
     else
-        step_body<Q, T, S, ACC>(p, b);
+        step_body<Q, T, S, ACC, NOISE>(p, b);
 }
 
-template <int Q, typename T, typename S, bool ACC>
+template <int Q, typename T, typename S, bool ACC, bool NOISE = false>
 __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(const StepArgs<T> p)
 {
-    step_cells_body<Q, T, S, ACC>(p, blockIdx.x);
+    step_cells_body<Q, T, S, ACC, NOISE>(p, blockIdx.x);
 }
 
 // Many lattices in one launch: the block finds its lattice by binary search
@@ -888,6 +992,12 @@ cudaError_t launch_q(const void *args, int mode, int nblocks, int bx, cudaStream
     case kModeStepAcc:
         if constexpr (Storage<S>::kRef)
             k_step<Q, T, S, true><<<nblocks, bx, 0, s>>>(a);
+        else
+            return cudaErrorInvalidValue;
+        break;
+    case kModeStepNoise:
+        if constexpr (!Storage<S>::kRef)
+            k_step<Q, T, S, false, true><<<nblocks, bx, 0, s>>>(a);
         else
             return cudaErrorInvalidValue;
         break;

@@ -378,7 +378,7 @@ __device__ __forceinline__ int thread_segment(const StepArgs<float> &p, bool wat
     return (water ? 0 : p.nseg_w) + row * p.nch32 + xs / 32;
 }
 
-template <int Q, typename S, bool ACC>
+template <int Q, typename S, bool ACC, bool NOISE = false>
 __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
 {
     const bool water = b < p.snbw;
@@ -413,7 +413,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     }
     const uint32_t xm = (uint32_t)src[19];
     const int4 q5 = __ldg(t4 + 5);  // xp, slot, nface, partner[0]
-    const int4 q7 = __ldg(t4 + 7);  // flags
+    const int4 q7 = __ldg(t4 + 7);  // flags, cs
     const uint32_t xp = (uint32_t)q5.x;
     const bool xbounce = (q7.x & kXBounce) != 0;
 
@@ -430,6 +430,11 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
             for (int a = 0; a < 3; ++a) store_u2(p.U0[kFluid] + (a * ns + q5.y) * nxp + X.x0, c.u[a], both);
         }
         collide2<Q>(g, c, j, p.rho0, p.om[0]);
+        if constexpr (NOISE) {
+            const uint32_t cell = (uint32_t)X.x0 + (uint32_t)p.nx * (uint32_t)q7.y;
+            thermal_noise<Q, float>(p, cell, [&](int i, float v) { g[i].x += v; });
+            if (both) thermal_noise<Q, float>(p, cell + 1, [&](int i, float v) { g[i].y += v; });
+        }
         if (live)
             store_pair<Q, S>(g, static_cast<S *>(p.out[0]), p.n_rows[kFluid] * nxp, row * nxp + X.x0, both,
                              ref_row<float, S>(p.enc_out[0], row), sc);

@@ -27,7 +27,7 @@ KLB_IFACE_SPECULAR, KLB_IFACE_BOUNCEBACK = 0, 1
 STATUS = {0: "KLB_OK", 1: "KLB_EINVAL", 2: "KLB_ENOMEM", 3: "KLB_ECUDA", 4: "KLB_EUNSTABLE",
           5: "KLB_ETIMEOUT", 6: "KLB_ESTATE"}
 EXPORTS = ["klb_lattice_bytes", "klb_lattice_info", "klb_create_lattice", "klb_set_couplings",
-           "klb_init_equilibrium", "klb_step", "klb_observables", "klb_observables_static",
+           "klb_set_fluctuations", "klb_init_equilibrium", "klb_step", "klb_observables", "klb_observables_static",
            "klb_get_field",
            "klb_get_state", "klb_set_state", "klb_get_step", "klb_species_cells",
            "klb_destroy", "klb_last_error", "klb_batch_bytes", "klb_batch_create",
