@@ -37,12 +37,14 @@ cudaError_t launch_ref(int Q, int storage, const void *args, float *const enc[3]
     return Q == 9 ? launch_ref_q9(args, enc, dec, s) : launch_ref_q19(args, enc, dec, s);
 }
 
-// Deterministic final reduction of the per-block partial sums (one block).
+// Deterministic final reduction of the per-block partial sums: block k
+// reduces sum k (strided per-thread sums in a fixed order, then a tree).
 __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ partials, int nblocks,
                                                   double *__restrict__ sums)
 {
     __shared__ double red[256];
-    for (int k = 0; k < kNumSums; ++k) {
+    {
+        const int k = blockIdx.x;
         const bool is_max = k == kSumResidual;
         double v = 0.0;
         for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ par
 
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s)
 {
-    k_finalize<<<1, 256, 0, s>>>(partials, nblocks, sums);
+    k_finalize<<<kNumSums, 256, 0, s>>>(partials, nblocks, sums);
     return cudaGetLastError();
 }
 

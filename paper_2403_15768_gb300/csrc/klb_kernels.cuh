@@ -383,21 +383,61 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
-__device__ inline void block_reduce_store(double (&s)[kNumSums], double *out)
+// Block sums of the observation pass (one row chunk per block, so the row
+// class and flags are block-uniform).  Only the sums that can be non-zero
+// for the block's class run a warp reduction (FP64 throughput on GB300 is a
+// small fraction of FP32); the slip-fit count and distance moments and the wall-row count
+// follow from the number of live cells and the row's d^2, the fit and
+// wall-row u_x sums are the u_x sum itself (every cell of such a row adds
+// its u_x to both), and non-finite values are counted with block-wide
+// predicate counts.  Each entry equals what a reduction of the per-cell
+// values gives.
+__device__ inline void observe_reduce_store(const double (&s)[kNumSums], bool water, int flags, double d2,
+                                            bool live, double *out)
 {
     __shared__ double red[kNumSums][kBlockX / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
+    const bool fit = water && (flags & kFitRow), wall = water && (flags & kWallRow);
+    const uint32_t sel =
+        water ? (1u << kSumUxFluid) | (1u << kSumMomW) | (1u << kSumMassW) | (1u << kSumResidual) |
+                    (fit ? (1u << kSumFitUD2) : 0u)
+              : (1u << kSumUxE) | (1u << kSumUxP) | (1u << kSumMomE) | (1u << kSumMomP) | (1u << kSumMassE) |
+                    (1u << kSumMassP) | (1u << kSumResidual);
+    const int cnt = __syncthreads_count(live);
+    const int nonfinite =
+        __syncthreads_count(s[kSumNonfinite] >= 1.0) + __syncthreads_count(s[kSumNonfinite] >= 2.0);
 #pragma unroll
     for (int k = 0; k < kNumSums; ++k) {
-        double v = (k == kSumResidual) ? warp_max(s[k]) : warp_sum(s[k]);
+        if (!((sel >> k) & 1u)) continue;
+        const double v = (k == kSumResidual) ? warp_max(s[k]) : warp_sum(s[k]);
         if (lane == 0) red[k][warp] = v;
     }
     __syncthreads();
     if (threadIdx.x < kNumSums) {
         const int k = threadIdx.x;
-        double v = red[k][0];
-        for (int w = 1; w < nwarps; ++w) v = (k == kSumResidual) ? fmax(v, red[k][w]) : v + red[k][w];
+        auto total = [&](int kk) {
+            double v = red[kk][0];
+            for (int w = 1; w < nwarps; ++w) v = (kk == kSumResidual) ? fmax(v, red[kk][w]) : v + red[kk][w];
+            return v;
+        };
+        double v = 0.0;
+        if ((sel >> k) & 1u)
+            v = total(k);
+        else if (k == kSumFitN)
+            v = fit ? (double)cnt : 0.0;
+        else if (k == kSumFitD2)
+            v = fit ? cnt * d2 : 0.0;
+        else if (k == kSumFitD4)
+            v = fit ? cnt * (d2 * d2) : 0.0;
+        else if (k == kSumFitU)
+            v = fit ? total(kSumUxFluid) : 0.0;
+        else if (k == kSumWallN)
+            v = wall ? (double)cnt : 0.0;
+        else if (k == kSumWallU)
+            v = wall ? total(kSumUxFluid) : 0.0;
+        else if (k == kSumNonfinite)
+            v = (double)nonfinite;
         out[k] = v;
     }
 }
@@ -537,7 +577,11 @@ __global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
             }
         }
     }
-    if (MODE == kModeObserve) block_reduce_store(s, p.partials + (size_t)b * kNumSums);
+    if (MODE == kModeObserve) {
+        const RowInfo &Rb = p.rows[water ? kFluid : kSolid][row];
+        observe_reduce_store(s, water, water ? Rb.flags : 0, (double)Rb.d2, live,
+                             p.partials + (size_t)b * kNumSums);
+    }
 }
 
 // Start from the local equilibrium of the fields (drho, u) staged in p.field
@@ -895,26 +939,23 @@ __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(con
     step_cells_body<Q, T, S, ACC, NOISE>(p, blockIdx.x);
 }
 
-// Many lattices in one launch: the block finds its lattice by binary search
-// over the block prefix and works from a shared-memory copy of that
-// lattice's arguments.
+// Many lattices in one launch: the block finds its lattice as the number of
+// lattices after the first whose first block is at or before its own
+// (prefix[] is increasing), counted by all threads at once — one round of
+// independent loads instead of a chain of dependent ones — and works from a
+// shared-memory copy of that lattice's arguments.
 template <int Q, typename T, typename S, bool ACC>
 __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>()))
     k_step_batch(const StepArgs<T> *__restrict__ table, const int *__restrict__ prefix, int n)
 {
     __shared__ StepArgs<T> sp;
     __shared__ int s_lid;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n - 1;  // last l with prefix[l] <= blockIdx.x
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(prefix + mid) <= (int)blockIdx.x)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        s_lid = lo;
-    }
+    if (threadIdx.x == 0) s_lid = 0;
+    __syncthreads();
+    int c = 0;
+    for (int m = 1 + (int)threadIdx.x; m < n; m += blockDim.x) c += __ldg(prefix + m) <= (int)blockIdx.x;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_lid, c);
     __syncthreads();
     const int lid = s_lid;
     static_assert(sizeof(StepArgs<T>) % 16 == 0, "argument record in 16-byte words");

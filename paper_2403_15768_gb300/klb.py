@@ -141,6 +141,8 @@ def load_library(path: str | None = None):
     lib.klb_create_lattice.argtypes = [ctypes.POINTER(klb_desc), P, SZ, P, ctypes.POINTER(P)]
     lib.klb_set_couplings.restype = I32
     lib.klb_set_couplings.argtypes = [P, ctypes.POINTER(klb_couplings)]
+    lib.klb_set_fluctuations.restype = I32
+    lib.klb_set_fluctuations.argtypes = [P, ctypes.c_double, ctypes.c_uint64]
     lib.klb_init_equilibrium.restype = I32
     lib.klb_init_equilibrium.argtypes = [P, P, P]
     lib.klb_step.restype = I32
@@ -273,6 +275,10 @@ class Lattice:
     def set_couplings(self, g_we, g_wp, g_ep, g_ec=0.0, g_pc=0.0):
         c = klb_couplings(g_we, g_wp, g_ep, g_ec, g_pc)
         _check(_lib.klb_set_couplings(self._h, ctypes.byref(c)), self._h)
+
+    def set_fluctuations(self, kT: float, seed: int = 0):
+        """Thermal noise of the water populations (klb_set_fluctuations)."""
+        _check(_lib.klb_set_fluctuations(self._h, float(kT), int(seed)), self._h)
 
     def init_equilibrium(self, drho=None, u=None):
         d = None if drho is None else np.ascontiguousarray(drho, np.float64)
