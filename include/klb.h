@@ -191,6 +191,18 @@ klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
  * deviations).  Host only; takes effect at the next step. */
 klb_status klb_set_couplings(klb_lattice *lat, const klb_couplings *c);
 
+/* Index checks of debug builds (no counterpart in the paper; they stand in
+ * for a memory checker).  A library compiled with -DKLB_BOUNDS=1
+ * (klb_bounds_checked() returns 1) checks, in every kernel that reads a row
+ * record, that the row, its source offsets, the thread's x positions and the
+ * interface slots index inside their arrays before anything is touched; a
+ * thread that fails records a site code (1 row, 2 source offset, 3 x,
+ * 4 slot, 5 partner slot, 6 face count) and skips its cells.
+ * klb_bounds_status returns the first recorded site of the lattice (0: none)
+ * and clears it; synchronises.  Normal builds never record anything. */
+klb_status klb_bounds_status(klb_lattice *lat, uint32_t *site);
+int klb_bounds_checked(void);
+
 /* Thermal fluctuations of the water (Eq. 6, the classical
  * fluctuation-dissipation relation of the momentum flux; Eq. 17, its
  * lattice source), in the standard fluctuating lattice Boltzmann form:

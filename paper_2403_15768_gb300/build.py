@@ -2,7 +2,9 @@
 
 Plain nvcc for sm_103a, one translation unit per source compiled in
 parallel, then one shared-library link.  No torch extension machinery: the
-library exposes only the C ABI of ``include/klb.h``.
+library exposes only the C ABI of ``include/klb.h``.  ``bounds=True``
+builds the debug variant with index checks (``-DKLB_BOUNDS=1``) into
+``_build_bounds/``.
 """
 from __future__ import annotations
 
@@ -34,23 +36,26 @@ def _inputs():
     return [os.path.join(CSRC, s) for s in SOURCES] + hdrs + [__file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), bounds: bool = False) -> str:
+    build_dir = BUILD + "_bounds" if bounds else BUILD
+    lib = os.path.join(build_dir, "libklb.so")
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
+    flags = [*extra_flags, *(["-DKLB_BOUNDS=1"] if bounds else [])]
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
-              "-I", os.path.join(ROOT, "include"), "-I", CSRC, *ARCH, *extra_flags]
+              "-I", os.path.join(ROOT, "include"), "-I", CSRC, *ARCH, *flags]
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.rsplit(".", 1)[0] + ".o")
+        obj = os.path.join(build_dir, src.rsplit(".", 1)[0] + ".o")
         objs.append(obj)
         cmd = [nvcc(), *common, "-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cu"):
@@ -62,11 +67,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             sys.stderr.write(out.decode(errors="replace"))
         if pr.returncode != 0:
             raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds="--bounds" in sys.argv))

@@ -17,6 +17,10 @@
 #include "klb.h"
 #include "klb_internal.h"
 
+#ifndef KLB_BOUNDS
+#define KLB_BOUNDS 0
+#endif
+
 using namespace klb;
 
 // Host view of the time level of a lattice: steps taken, buffer holding the
@@ -141,6 +145,7 @@ void fill_args_at(const klb_lattice *L, const HostState &st, int sbx, StepArgs<T
     a.key[1] = (uint32_t)(L->seed >> 32);
     a.step_lo = (uint32_t)((uint64_t)n & 0xffffffffu);
     a.step_hi = (uint32_t)((uint64_t)n >> 32);
+    a.bounds_err = (unsigned *)dev(L, p.bounds);
 }
 
 template <typename T>
@@ -404,6 +409,7 @@ klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
         e = cudaMemcpyAsync(dev(L, L->plan.rows[c]), L->geo.info[c].data(),
                             sizeof(RowInfo) * L->geo.info[c].size(), cudaMemcpyHostToDevice,
                             L->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dev(L, L->plan.bounds), 0, sizeof(unsigned), L->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(L->stream);
     if (e != cudaSuccess) {
         std::string m = std::string("uploading row tables: ") + cudaGetErrorString(e);
@@ -419,6 +425,20 @@ klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
     *out = L;
     return KLB_OK;
 }
+
+klb_status klb_bounds_status(klb_lattice *L, uint32_t *site)
+{
+    if (!L || !site) return fail(L, KLB_EINVAL, "null argument");
+    unsigned w = 0;
+    KLB_CUDA(L, cudaMemcpyAsync(&w, dev(L, L->plan.bounds), sizeof w, cudaMemcpyDeviceToHost, L->stream));
+    KLB_CUDA(L, cudaMemsetAsync(dev(L, L->plan.bounds), 0, sizeof w, L->stream));
+    klb_status st = sync(L);
+    if (st != KLB_OK) return st;
+    *site = w;
+    return KLB_OK;
+}
+
+int klb_bounds_checked(void) { return KLB_BOUNDS; }
 
 klb_status klb_set_fluctuations(klb_lattice *L, double kT, uint64_t seed)
 {

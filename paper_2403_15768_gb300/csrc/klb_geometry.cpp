@@ -340,6 +340,7 @@ MemoryPlan plan_memory(const Geometry &g, int storage)
         p.acc_bytes = sizeof(float) * 2 * g.Q * nseg;
         p.acc = take(p.acc_bytes);
     }
+    p.bounds = take(sizeof(unsigned));
     p.total = off;
     return p;
 }

@@ -91,6 +91,7 @@ struct MemoryPlan {
     size_t ref_enc[2][3], ref_dec[2][3];  // [generation][species], reduced storage only
     size_t ref_bytes[3];
     size_t acc, acc_bytes;
+    size_t bounds;         // error word of debug builds (KLB_BOUNDS)
     size_t total;
     int nblocks_w, nblocks_s, nchunk, bx;  // one cell per thread (observe, field, init)
     int sbx, snblocks;                     // step kernel: threads per block, blocks
@@ -154,6 +155,7 @@ struct alignas(16) StepArgs {
     T noise_amp;           // sqrt(3 rho0 kT omega (2 - omega))
     uint32_t key[2];       // generator key (seed)
     uint32_t step_lo, step_hi;  // the step being taken
+    unsigned *bounds_err;  // debug builds: first out-of-range index site
 };
 
 enum Mode {

@@ -39,6 +39,10 @@
 
 #include "klb_internal.h"
 
+#ifndef KLB_BOUNDS
+#define KLB_BOUNDS 0
+#endif
+
 namespace klb {
 
 // ---------------------------------------------------------------------------
@@ -362,6 +366,42 @@ __device__ __forceinline__ void solid_math(const StepArgs<T> &p, const T *Uw1, c
 }
 
 // ---------------------------------------------------------------------------
+// Debug builds (-DKLB_BOUNDS=1; the sanitiser is not available) check, before
+// a thread touches anything, that every index it will derive from its row
+// record lies inside its array: the row, the Q source offsets (whole rows of
+// the population array), the x positions (inside the padded row), the
+// interface slot and the partner slots.  A failure records its site in the
+// lattice's error word (klb_bounds_status) and the thread continues on row 0
+// as a dead thread, touching only valid memory.  Normal builds compile
+// nothing of this.
+enum BoundsSite { kBadRow = 1, kBadSource = 2, kBadX = 3, kBadSlot = 4, kBadPartner = 5, kBadFaces = 6 };
+
+template <int Q, typename T>
+__device__ __noinline__ bool row_indices_ok(const StepArgs<T> &p, bool water, int row, int xmin, int xmax)
+{
+    const int cls = water ? kFluid : kSolid, other = 1 - cls;
+    unsigned site = 0;
+    if (row < 0 || row >= p.n_rows[cls]) {
+        site = kBadRow;
+    } else if (xmin < 0 || xmax >= p.nxp) {
+        site = kBadX;
+    } else {
+        const RowInfo &R = p.rows[cls][row];
+        const long long hi = (long long)(Q * p.n_rows[cls] - 1) * p.nxp;
+        for (int i = 0; i < Q && !site; ++i) {
+            const int v = R.src[i];
+            if (v < 0 || v > hi || v % p.nxp) site = kBadSource;
+        }
+        if (!site && R.slot >= p.n_slots[cls]) site = kBadSlot;
+        if (!site && (R.nface < 0 || R.nface > kMaxFaces)) site = kBadFaces;
+        for (int k = 0; !site && k < R.nface; ++k)
+            if (R.slot >= 0 && (R.partner[k] < 0 || R.partner[k] >= p.n_slots[other])) site = kBadPartner;
+    }
+    if (site) atomicCAS(p.bounds_err, 0u, site);
+    return site == 0;
+}
+
+// ---------------------------------------------------------------------------
 // Block reductions (fixed order).
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -481,9 +521,15 @@ __global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
     const int b = blockIdx.x;
     const bool water = b < p.nbw;
     const int bb = water ? b : b - p.nbw;
-    const int row = bb / p.nchunk;
+    int row = bb / p.nchunk;
     const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
-    const bool live = x < p.nx;
+    bool live = x < p.nx;
+    if constexpr (KLB_BOUNDS) {
+        if (live && !row_indices_ok<Q>(p, water, row, 0, x)) {
+            live = false;
+            row = 0;
+        }
+    }
     const float inv = p.inv_scale;
 
     double s[kNumSums];
@@ -595,9 +641,15 @@ __global__ void __launch_bounds__(kBlockX) k_init(const StepArgs<T> p)
     const int b = blockIdx.x;
     const bool water = b < p.nbw;
     const int bb = water ? b : b - p.nbw;
-    const int row = bb / p.nchunk;
+    int row = bb / p.nchunk;
     const int x = (bb - row * p.nchunk) * blockDim.x + threadIdx.x;
-    const bool live = x < p.nx;
+    bool live = x < p.nx;
+    if constexpr (KLB_BOUNDS) {
+        if (live && !row_indices_ok<Q>(p, water, row, x, x)) {
+            live = false;
+            row = 0;
+        }
+    }
     const int nxp = p.nxp;
     const int nrw = p.n_rows[kFluid], nrs = p.n_rows[kSolid];
     const int cls = water ? kFluid : kSolid;
@@ -811,10 +863,16 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
     const bool water = b < p.snbw;
     const int bb = water ? b : b - p.snbw;
     const int nch = water ? p.snchunk_w : p.snchunk_s;
-    const int row = bb / nch;
+    int row = bb / nch;
     int x = (bb - row * nch) * blockDim.x + threadIdx.x;
     const int x_lane = x;
-    const bool live = x < p.nx;
+    bool live = x < p.nx;
+    if constexpr (KLB_BOUNDS) {
+        if (live && !row_indices_ok<Q>(p, water, row, 0, x)) {
+            live = false;
+            row = 0;
+        }
+    }
     if constexpr (!ACC) {
         if (!live) return;  // no warp-wide operation follows
     } else {

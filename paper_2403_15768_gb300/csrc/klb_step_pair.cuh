@@ -384,10 +384,16 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     const bool water = b < p.snbw;
     const int bb = water ? b : b - p.snbw;
     const int nch = water ? p.snchunk_w : p.snchunk_s;
-    const int row = bb / nch;
+    int row = bb / nch;
     const int xt = (bb - row * nch) * blockDim.x + threadIdx.x;
     const int x_first = 2 * xt;
-    const bool live = x_first < p.nx;
+    bool live = x_first < p.nx;
+    if constexpr (KLB_BOUNDS) {
+        if (live && !row_indices_ok<Q>(p, water, row, 0, x_first + 1)) {
+            live = false;
+            row = 0;
+        }
+    }
     if constexpr (!ACC) {
         if (!live) return;  // no warp-wide operation follows
     }

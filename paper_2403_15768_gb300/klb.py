@@ -27,7 +27,7 @@ KLB_IFACE_SPECULAR, KLB_IFACE_BOUNCEBACK = 0, 1
 STATUS = {0: "KLB_OK", 1: "KLB_EINVAL", 2: "KLB_ENOMEM", 3: "KLB_ECUDA", 4: "KLB_EUNSTABLE",
           5: "KLB_ETIMEOUT", 6: "KLB_ESTATE"}
 EXPORTS = ["klb_lattice_bytes", "klb_lattice_info", "klb_create_lattice", "klb_set_couplings",
-           "klb_set_fluctuations", "klb_init_equilibrium", "klb_step", "klb_observables", "klb_observables_static",
+           "klb_set_fluctuations", "klb_bounds_status", "klb_bounds_checked", "klb_init_equilibrium", "klb_step", "klb_observables", "klb_observables_static",
            "klb_get_field",
            "klb_get_state", "klb_set_state", "klb_get_step", "klb_species_cells",
            "klb_destroy", "klb_last_error", "klb_batch_bytes", "klb_batch_create",
@@ -131,7 +131,7 @@ def load_library(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    lib = ctypes.CDLL(path or _build.build())
+    lib = ctypes.CDLL(path or os.environ.get("KLB_LIBRARY") or _build.build())
     P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     lib.klb_lattice_bytes.restype = SZ
     lib.klb_lattice_bytes.argtypes = [ctypes.POINTER(klb_desc)]
@@ -141,6 +141,10 @@ def load_library(path: str | None = None):
     lib.klb_create_lattice.argtypes = [ctypes.POINTER(klb_desc), P, SZ, P, ctypes.POINTER(P)]
     lib.klb_set_couplings.restype = I32
     lib.klb_set_couplings.argtypes = [P, ctypes.POINTER(klb_couplings)]
+    lib.klb_bounds_status.restype = I32
+    lib.klb_bounds_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint32)]
+    lib.klb_bounds_checked.restype = ctypes.c_int
+    lib.klb_bounds_checked.argtypes = []
     lib.klb_set_fluctuations.restype = I32
     lib.klb_set_fluctuations.argtypes = [P, ctypes.c_double, ctypes.c_uint64]
     lib.klb_init_equilibrium.restype = I32
@@ -275,6 +279,13 @@ class Lattice:
     def set_couplings(self, g_we, g_wp, g_ep, g_ec=0.0, g_pc=0.0):
         c = klb_couplings(g_we, g_wp, g_ep, g_ec, g_pc)
         _check(_lib.klb_set_couplings(self._h, ctypes.byref(c)), self._h)
+
+    def bounds_status(self) -> int:
+        """First out-of-range index site recorded by a debug build (0: none);
+        clears it."""
+        v = ctypes.c_uint32()
+        _check(_lib.klb_bounds_status(self._h, ctypes.byref(v)), self._h)
+        return v.value
 
     def set_fluctuations(self, kT: float, seed: int = 0):
         """Thermal noise of the water populations (klb_set_fluctuations)."""

@@ -161,3 +161,7 @@ def test_request_stream_recipe():
         info = klb.klb_lattice_info(klb.desc_from_workload(w))
         assert info["active_sites"] > 0
     assert {r.w.geom for r in rs} == {"slab", "pipe"}
+
+
+def test_normal_build_has_no_index_checks():
+    assert klb.load_library().klb_bounds_checked() == 0
