@@ -18,6 +18,9 @@ Other workloads (--workload):
   serving_{fp32,fp16}  a seeded Poisson stream of design-sweep requests
       replayed against the request loop (--steps = requests); reports
       aggregate MLUPS and p50/p99 time to solution.
+  design_map  pipes of radius 8..48 x water-electron couplings -0.02..0.05
+      run to steady state through the request loop; reports aggregate MLUPS
+      and the map of slip length, flow enhancement and electron wind.
 
 Metric: MLUPS = active lattice sites (fluid + solid cells) updated per
 second, whole job.  With N GPUs (torchrun) every rank runs its own replica
@@ -204,6 +207,8 @@ def run(args):
         return run_sweep(args)
     if args.workload.startswith("serving_"):
         return run_serving(args)
+    if args.workload == "design_map":
+        return run_design_map(args)
     import torch
 
     from paper_2403_15768_gb300 import inputs, klb
@@ -478,8 +483,61 @@ def run_serving(args):
         dist.destroy_process_group()
 
 
+def run_design_map(args):
+    """A design map of the nanotube permeability study's shape: pipes of
+    radius 8..48 for water-electron couplings -0.02 .. 0.05 (negative quantum
+    friction included), each run from rest to steady state through the
+    request loop; reports aggregate MLUPS and the map."""
+    import torch
+
+    from paper_2403_15768_gb300 import inputs, klb, serving
+
+    rank, local, world, dist = _dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ws = inputs.design_grid(range(8, 49, 8), [-0.02, 0.0, 0.02, 0.05])
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        srv = klb.Server(32 * 10 ** 9, storage="fp32", check_every=200, max_resident=64, device=dev,
+                         stream=stream)
+        serving.design_map(srv, ws[:2], tol=1e-6, max_steps=400)  # warm-up
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            res = serving.design_map(srv, ws, tol=1e-9, max_steps=100_000)
+            wall = time.perf_counter() - t0
+        rounds = srv.stats()["rounds"]
+        srv.close()
+    updates = float(sum(r["sites"] * r["steps"] for r in res))
+    if dist is not None:
+        t = torch.tensor([wall, updates], device=dev, dtype=torch.float64)
+        mk = t.clone()
+        dist.all_reduce(mk, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        wall, updates = float(mk[0]), float(t[1])
+    if rank != 0:
+        return
+    value = updates / wall / 1e6
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": len(ws),
+        "warmup": 2, "ms_per_step": 1e3 * wall / len(ws), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "design map: D3Q19 pipes R = 8..48 x g_we = -0.02..0.05, FP32, tol 1e-9",
+                   "requests": len(ws), "parallelism": f"replicas x{world}"},
+        "map": [[r["radius"], r["g_we"], r["slip_length"], r["enhancement"], r["mean_u_e"], r["steps"],
+                 r["status"]] for r in res],
+        "roofline": None,
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "requests enter and results leave through the host API; wall time"},
+        "gpu_launches": int(rounds * 200),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 WORKLOADS = ["nanotube", "nanotube_large_fp32", "nanotube_large_fp16", "nanotube_large_bf16",
-             "sweep_fp32", "sweep_fp16", "serving_fp32", "serving_fp16"]
+             "sweep_fp32", "sweep_fp16", "serving_fp32", "serving_fp16", "design_map"]
 
 
 def main():

@@ -173,3 +173,21 @@ def request_stream(n: int, rate: float = 50.0, seed: int = 0, storage: str = "fp
             w = Workload(geom="slab", width=ny - 2 * shell, **common)
         out.append(Request(k, t, w))
     return out
+
+
+def design_grid(radii, g_we_values, nx: int = 8, shell: int = 3, tau_w: float = 0.8, G: float = 1e-6,
+                g_wp: float = 0.05, g_ep: float = 0.1, g_pc: float = 0.01, storage: str = "fp32"):
+    """Pipes of the given radii (box 2 (R + shell) + 2 square, nx x planes,
+    x-invariant) for each water-electron coupling g_we (negative values: the
+    negative quantum friction of Sec. 2): the shape of the nanotube
+    permeability study of Sec. 5.1.  Other couplings fixed; g_ec = 0.  A
+    steady state needs net wall friction, g_we + g_wp > 0 (with
+    g_we + g_wp = 0 the water accelerates freely)."""
+    out = []
+    for R in radii:
+        for g in g_we_values:
+            n = 2 * (R + shell) + 2
+            out.append(Workload(name=f"map_R{R}_g{g:+.3f}", kind=19, geom="pipe", nx=nx, ny=n, nz=n,
+                                radius=R, shell=shell, tau=(tau_w, 0.6, 1.0), G=(G, 0.0, 0.0),
+                                couplings=(float(g), g_wp, g_ep, 0.0, g_pc), storage=storage))
+    return out

@@ -66,3 +66,30 @@ def summarise(run: dict) -> dict:
             "wait_p99_s": float(np.percentile(wait, 99)),
             "mlups": updates / max(last - first, 1e-9) / 1e6, "site_updates": updates,
             "status": status, "makespan_s": last - first}
+
+
+def design_map(server: "klb.Server", workloads, tol: float, max_steps: int) -> list:
+    """Run every workload (a design grid, e.g. inputs.design_grid) from rest
+    to its steady state through the request loop and return, per workload,
+    the status, steps, slip length, flow rate per unit length, the flow
+    enhancement over the no-slip Poiseuille flow of the same effective radius
+    (pi G d_wall^4 / (8 rho0 nu)) and the mean electron and phonon
+    velocities (the electron and phonon winds)."""
+    for k, w in enumerate(workloads):
+        server.submit(klb.desc_from_workload(w), w.couplings, tol, max_steps, k)
+    done = {}
+    while len(done) < len(workloads):
+        server.tick()
+        for res in server.poll():
+            done[res["id"]] = res
+    out = []
+    for k, w in enumerate(workloads):
+        r = done[k]
+        o = r["obs"]
+        nu = (w.tau[0] - 0.5) / 3.0
+        q0 = np.pi * w.G[0] * o["d_wall"] ** 4 / (8.0 * w.rho0 * nu)
+        out.append({"name": w.name, "radius": w.radius, "g_we": w.couplings[0], "status": r["status"],
+                    "steps": r["steps"], "slip_length": o["slip_length"], "flow_rate": o["flow_rate"],
+                    "enhancement": o["flow_rate"] / q0, "mean_u_e": o["mean_u"][1],
+                    "mean_u_p": o["mean_u"][2], "sites": r["sites"]})
+    return out

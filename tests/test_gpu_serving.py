@@ -103,3 +103,41 @@ def test_replay_reports_latencies():
     assert s["finished"] == len(STREAM) and s["p99_s"] >= s["p50_s"] > 0 and s["mlups"] > 0
     for r in run["results"]:
         assert r["arrival"] <= r["admitted"] <= r["finished"]
+
+
+def test_design_map_matches_oracle_steady_states():
+    """A small design map (pipes of radius 6 and 8, water-electron friction
+    -0.02 and +0.05) run to steady state through the request loop in FP64
+    equals the oracle's steady states: slip length, flow rate and electron
+    wind."""
+    from klb_testutil import make_oracle
+    from oracle import observables_from_fields
+
+    ws = inputs.design_grid([6, 8], [-0.02, 0.05], nx=2, shell=2, storage="fp64")
+    srv = klb.Server(64 * 1024 * 1024, storage="fp64", check_every=500, max_resident=8)
+    res = serving.design_map(srv, ws, tol=1e-13, max_steps=300_000)
+    srv.close()
+    for w, r in zip(ws, res):
+        assert r["status"] == 0, r
+        o = make_oracle(w, nx=1)
+        o.init_equilibrium()
+        prev = None
+        for _ in range(150):
+            o.step(2000)
+            f = o.observe()
+            if prev is not None and np.abs(f["u"] - prev).max() < 1e-14 * np.abs(f["u"]).max():
+                break
+            prev = f["u"]
+        else:
+            raise AssertionError("oracle not steady")
+        ob = observables_from_fields(o.geo, 1, w.rho0, f)
+        assert r["slip_length"] == pytest.approx(ob["slip_length"], rel=1e-6)
+        assert r["flow_rate"] == pytest.approx(ob["flow_rate"], rel=1e-8)
+        ue = f["u"][1][0][species_solid(o.geo)].mean()
+        assert r["mean_u_e"] == pytest.approx(ue, rel=1e-6)
+    # the negative coupling changes the slip: the map is not flat in g_we
+    assert res[0]["slip_length"] != pytest.approx(res[1]["slip_length"], rel=1e-3)
+
+
+def species_solid(geo):
+    return np.broadcast_to((geo.cs_type == 2)[:, :, None], (geo.nz, geo.ny, 1))
