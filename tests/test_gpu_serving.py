@@ -115,7 +115,7 @@ def test_design_map_matches_oracle_steady_states():
 
     ws = inputs.design_grid([6, 8], [-0.02, 0.05], nx=2, shell=2, storage="fp64")
     srv = klb.Server(64 * 1024 * 1024, storage="fp64", check_every=500, max_resident=8)
-    res = serving.design_map(srv, ws, tol=1e-13, max_steps=300_000)
+    res = serving.design_map(srv, ws, tol=1e-16, max_steps=300_000)
     srv.close()
     for w, r in zip(ws, res):
         assert r["status"] == 0, r
@@ -132,7 +132,7 @@ def test_design_map_matches_oracle_steady_states():
             raise AssertionError("oracle not steady")
         ob = observables_from_fields(o.geo, 1, w.rho0, f)
         assert r["slip_length"] == pytest.approx(ob["slip_length"], rel=1e-6)
-        assert r["flow_rate"] == pytest.approx(ob["flow_rate"], rel=1e-8)
+        assert r["flow_rate"] == pytest.approx(ob["flow_rate"], rel=1e-7)
         ue = f["u"][1][0][species_solid(o.geo)].mean()
         assert r["mean_u_e"] == pytest.approx(ue, rel=1e-6)
     # the negative coupling changes the slip: the map is not flat in g_we
