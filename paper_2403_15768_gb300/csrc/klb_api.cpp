@@ -500,6 +500,32 @@ klb_status klb_step(klb_lattice *L, int64_t nsteps)
     return KLB_OK;
 }
 
+}  // extern "C"
+
+// Observation of many lattices with one synchronisation (the request loop):
+// enqueue each lattice's pass and the copy of its sums to pinned host memory,
+// synchronise the shared stream once, then finish each from its sums.
+cudaError_t klb::observe_enqueue(klb_lattice *L, double *host_sums)
+{
+    cudaError_t e = with_args(L, [&](void *a) {
+        return launch(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L), L->plan.bx, L->stream);
+    });
+    if (e == cudaSuccess)
+        e = launch_finalize((const double *)dev(L, L->plan.partials), nblocks(L), (double *)dev(L, L->plan.sums),
+                            L->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_sums, dev(L, L->plan.sums), sizeof(double) * kNumSums, cudaMemcpyDeviceToHost,
+                            L->stream);
+    return e;
+}
+
+klb_status klb::observe_finish(klb_lattice *L, const double *host_sums, klb_obs *out)
+{
+    return finish_observables(L, host_sums, out);
+}
+
+extern "C" {
+
 klb_status klb_observables(klb_lattice *L, klb_obs *out)
 {
     if (!L || !out) return fail(L, KLB_EINVAL, "null argument");

@@ -113,6 +113,7 @@ struct klb_server {
     klb_batch *batch = nullptr;
     bool reform = false;
     std::deque<klb_result> done;
+    double *host_sums = nullptr;  // pinned, max_resident x kNumSums (retirement checks)
     klb_server_stats stats{};
     std::chrono::steady_clock::time_point t0;
     std::string err;
@@ -167,10 +168,26 @@ klb_status retire(klb_server *S)
     std::vector<klb_obs> obs(S->res.size());
     std::vector<char> leave(S->res.size(), 0);
     const double t = now(S);
+    // every resident lattice runs on the server's stream: enqueue all
+    // observation passes, synchronise once
+    if (!S->host_sums && !S->res.empty()) {
+        const size_t bytes = sizeof(double) * klb::kNumSums * (size_t)S->o.max_resident;
+        if (cudaMallocHost((void **)&S->host_sums, bytes) != cudaSuccess) {
+            S->host_sums = nullptr;
+            return sfail(S, KLB_ECUDA, "pinned host memory for the retirement checks");
+        }
+    }
+    for (size_t k = 0; k < S->res.size(); ++k) {
+        const cudaError_t e = klb::observe_enqueue(S->res[k].L, S->host_sums + k * klb::kNumSums);
+        if (e != cudaSuccess) return sfail(S, KLB_ECUDA, std::string("observation: ") + cudaGetErrorString(e));
+    }
+    if (!S->res.empty()) {
+        const cudaError_t e = cudaStreamSynchronize(S->stream);
+        if (e != cudaSuccess) return sfail(S, KLB_ECUDA, std::string("observation: ") + cudaGetErrorString(e));
+    }
     for (size_t k = 0; k < S->res.size(); ++k) {
         Resident &r = S->res[k];
-        const klb_status st = klb_observables(r.L, &obs[k]);
-        if (st == KLB_ECUDA) return sfail(S, st, std::string("observables: ") + klb_last_error(r.L));
+        const klb_status st = klb::observe_finish(r.L, S->host_sums + k * klb::kNumSums, &obs[k]);
         const int64_t steps = klb_get_step(r.L);
         if (st != KLB_OK) {
             verdict[k] = st;  // KLB_EUNSTABLE
@@ -364,6 +381,7 @@ klb_status klb_server_destroy(klb_server *S)
     drop_batch(S);
     for (Resident &r : S->res)
         if (r.L) klb_destroy(r.L);
+    if (S->host_sums) cudaFreeHost(S->host_sums);
     delete S;
     return KLB_OK;
 }
