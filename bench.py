@@ -16,8 +16,9 @@ Other workloads (--workload):
       benchmark step = 384 lattice steps of every channel + the observation
       pass of every channel.
   serving_{fp32,fp16}  a seeded Poisson stream of design-sweep requests
-      replayed against the request loop (--steps = requests); reports
-      aggregate MLUPS and p50/p99 time to solution.
+      (--rate per second, default 50) replayed against the request loop
+      (--steps = requests); reports aggregate MLUPS and p50/p99 time to
+      solution.
   design_map  pipes of radius 8..48 x water-electron couplings -0.02..0.05
       run to steady state through the request loop; reports aggregate MLUPS
       and the map of slip length, flow enhancement and electron wind.
@@ -446,7 +447,7 @@ def run_serving(args):
             warm = inputs.request_stream(args.warmup, rate=50.0, seed=1000 + rank, storage=storage,
                                          max_cells=64 ** 3)
             serving.replay(srv, warm, tol=tol, max_steps=2000)
-        reqs = inputs.request_stream(args.steps, rate=50.0, seed=rank, storage=storage)
+        reqs = inputs.request_stream(args.steps, rate=args.rate, seed=rank, storage=storage)
         with ClockSampler(local) as clk:
             run = serving.replay(srv, reqs, tol=tol, max_steps=max_steps)
     summ = serving.summarise(run)
@@ -466,7 +467,8 @@ def run_serving(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * summ["makespan_s"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"Poisson request stream, 50/s, seed = rank, {storage}",
+        "config": {"workload": f"Poisson request stream, {args.rate:g}/s, seed = rank, {storage}",
+                   "rate_per_s": args.rate,
                    "storage": storage, "requests": args.steps, "tol": tol, "max_steps": max_steps,
                    "check_every": 100, "arena_bytes": arena, "parallelism": f"replicas x{world}"},
         "serving": {k: summ[k] for k in ("p50_s", "p99_s", "mean_s", "wait_p50_s", "wait_p99_s",
@@ -547,6 +549,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="nanotube", choices=WORKLOADS)
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: requests per second")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 48 if args.workload.startswith("serving_") else (
