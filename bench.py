@@ -129,6 +129,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _allreduce(dist, values, op, device):
+    """Combine per-rank floats across ranks ("max": the slowest rank's time;
+    "sum": work of all ranks); identity without a process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(v) for v in t]
+
+
 def _dist_setup(gpus):
     import torch
     if gpus > 1 or "RANK" in os.environ:
@@ -271,12 +283,7 @@ def run(args):
     barrier()
     e2e_s = time.perf_counter() - t0
 
-    if dist is not None:
-        t = torch.tensor([ms, e2e_s * 1e3], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
-    else:
-        e2e_ms = e2e_s * 1e3
+    ms, e2e_ms = _allreduce(dist, [ms, e2e_s * 1e3], "max", dev)
 
     if rank != 0:
         return
@@ -386,10 +393,7 @@ def run_sweep(args):
             obs_e2e = [l.observables() for l in lats]
         barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3
-    if dist is not None:
-        t = torch.tensor([ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = _allreduce(dist, [ms, e2e_ms], "max", dev)
     if rank != 0:
         return
     updates = sites * SWEEP_STEPS * args.steps * world
@@ -452,12 +456,8 @@ def run_serving(args):
             run = serving.replay(srv, reqs, tol=tol, max_steps=max_steps)
     summ = serving.summarise(run)
     srv.close()
-    if dist is not None:
-        t = torch.tensor([summ["makespan_s"], summ["site_updates"]], device=dev, dtype=torch.float64)
-        mk = t.clone()
-        dist.all_reduce(mk, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        summ["makespan_s"], summ["site_updates"] = float(mk[0]), float(t[1])
+    summ["makespan_s"] = _allreduce(dist, [summ["makespan_s"]], "max", dev)[0]
+    summ["site_updates"] = _allreduce(dist, [summ["site_updates"]], "sum", dev)[0]
     if rank != 0:
         return
     value = summ["site_updates"] / summ["makespan_s"] / 1e6
@@ -510,12 +510,8 @@ def run_design_map(args):
         rounds = srv.stats()["rounds"]
         srv.close()
     updates = float(sum(r["sites"] * r["steps"] for r in res))
-    if dist is not None:
-        t = torch.tensor([wall, updates], device=dev, dtype=torch.float64)
-        mk = t.clone()
-        dist.all_reduce(mk, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        wall, updates = float(mk[0]), float(t[1])
+    wall = _allreduce(dist, [wall], "max", dev)[0]
+    updates = _allreduce(dist, [updates], "sum", dev)[0]
     if rank != 0:
         return
     value = updates / wall / 1e6
