@@ -798,7 +798,7 @@ klb_status klb_set_state(klb_lattice *L, const double *gin, const double *U1, co
             std::vector<float> dec(nr * kRefStride, 0.f);
             for (size_t r = 0; r < nr; ++r)
                 for (int i = 0; i < Q; ++i) {
-                    const long q = g.info[c][r].src[i] / g.nxp;  // sdir * nr + srow
+                    const long q = g.info[c][r].src[i] / (g.nxp / kRowAlign);  // sdir * nr + srow
                     const long sdir = q / (long)nr, srow = q - sdir * (long)nr;
                     dec[r * kRefStride + i] = enc[s][srow * kRefStride + sdir];
                 }

@@ -168,9 +168,17 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
     }
     if (g.rows[kFluid].empty()) return err = "geometry has no fluid cells", false;
     if (g.rows[kSolid].empty()) return err = "geometry has no solid cells", false;
+    // Index widths: a cell of the box is a 32-bit number x + nx (y + ny z);
+    // offsets within one direction plane (row * nxp + x) and within the
+    // interface-velocity buffers are 32-bit; row sources count in kRowAlign
+    // units of a class buffer (Q planes).  Larger class buffers than 2^31
+    // elements are fine: plane strides are 64-bit in the kernels.
+    if ((double)d.nx * d.ny * d.nz >= 4294967296.0)
+        return err = "box too large for 32-bit cell indices", false;
     for (int cls = 0; cls < 2; ++cls) {
-        double elems = (double)g.Q * g.rows[cls].size() * g.nxp;
-        if (elems >= 2147483647.0) return err = "lattice too large for 32-bit row offsets", false;
+        const double plane = (double)g.rows[cls].size() * g.nxp;
+        if (plane >= 2147483648.0 || (double)g.Q * plane / kRowAlign >= 2147483648.0)
+            return err = "lattice too large for 32-bit row offsets", false;
     }
 
     // ---- interface faces and slots
@@ -199,6 +207,9 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
             g.max_faces[cls] = std::max(g.max_faces[cls], (int)ri.nface);
         }
     }
+    for (int cls = 0; cls < 2; ++cls)
+        if ((cls == kFluid ? 3.0 : 6.0) * g.slot_row[cls].size() * g.nxp >= 2147483648.0)
+            return err = "lattice too large for 32-bit interface offsets", false;
     // partner cross-section index -> partner slot
     for (int cls = 0; cls < 2; ++cls)
         for (RowInfo &ri : g.info[cls])
@@ -245,7 +256,7 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
                 }
                 int srow = g.row_of_cs[cls][cs.index(sy, sz)];
                 if (srow < 0 || sdir < 0) return err = "internal: streaming source off the species", false;
-                ri.src[i] = (int32_t)(((long)sdir * nr + srow) * g.nxp);
+                ri.src[i] = (int32_t)(((long)sdir * nr + srow) * (g.nxp / kRowAlign));
                 if (sx == 1) ri.xm |= 1u << i;   // source at x - 1
                 if (sx == -1) ri.xp |= 1u << i;  // source at x + 1
                 if (cx != 0 && sx == 0) ri.flags |= kXBounce;
@@ -255,7 +266,7 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
         std::vector<uint8_t> used((size_t)g.Q * nr, 0);
         for (int r = 0; r < nr; ++r)
             for (int i = 0; i < g.Q; ++i) {
-                long e = g.info[cls][r].src[i] / g.nxp;
+                long e = g.info[cls][r].src[i] / (g.nxp / kRowAlign);
                 if (used[e]++) return err = "boundary rule is not a permutation for this geometry", false;
             }
     }

@@ -14,6 +14,10 @@ namespace klb {
 
 constexpr int kMaxFaces = 4;   // fluid/solid faces of one cross-section cell (+-y, +-z)
 constexpr int kBlockX = 128;   // threads per block along x (one x per thread)
+// Rows are padded to a multiple of kRowAlign elements.  RowInfo::src counts
+// in these units, so a 32-bit entry reaches 2^31 * 32 elements of a class
+// buffer; offsets within one direction plane (row * nxp + x) stay 32-bit.
+constexpr int kRowAlign = 32;
 
 // Row classes: a row is one cross-section cell together with all its x.
 // Water lives on fluid rows; electrons and phonons share the solid rows.
@@ -21,8 +25,8 @@ enum RowClass { kFluid = 0, kSolid = 1 };
 
 // Per-row table, read once per block (all threads of a block share a row).
 struct RowInfo {
-    int32_t src[19];            // element offset (dir' * n_rows + row') * nxp of the
-                                // row that direction i is pulled from
+    int32_t src[19];            // (dir' * n_rows + row') * nxp / kRowAlign: first element,
+                                // in kRowAlign units, of the row direction i is pulled from
     uint32_t xm;                // bit i: pull direction i from x - 1
     uint32_t xp;                // bit i: pull direction i from x + 1
     int32_t slot;               // interface slot of this row, -1 if none

@@ -248,7 +248,7 @@ __device__ __forceinline__ void collide(T g[Q], const Cell<T> &c, const T j[3], 
     }
 }
 
-// Store g* of one cell: out[i * row_stride + base], encoded against the
+// Store g* of one cell: out[i * row_stride + base] (64-bit plane offsets), encoded against the
 // row's references `enc` for reduced-precision storage.
 template <int Q, typename T, typename S>
 __device__ __forceinline__ void store_cell(const T g[Q], S *__restrict__ out, int row_stride,
@@ -257,10 +257,18 @@ __device__ __forceinline__ void store_cell(const T g[Q], S *__restrict__ out, in
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if constexpr (Storage<S>::kRef)
-            Storage<S>::store(out + i * row_stride + base, (float(g[i]) - __ldg(enc + i)) * scale);
+            Storage<S>::store(out + (long long)i * row_stride + base, (float(g[i]) - __ldg(enc + i)) * scale);
         else
-            Storage<S>::store(out + i * row_stride + base, g[i]);
+            Storage<S>::store(out + (long long)i * row_stride + base, g[i]);
     }
+}
+
+// First element of the source row of a RowInfo::src entry (kRowAlign units:
+// the product is 64-bit, so class buffers may exceed 2^31 elements).
+template <typename S>
+__device__ __forceinline__ const S *src_row(const S *in, int src)
+{
+    return in + (long long)src * kRowAlign;
 }
 
 template <typename T>
@@ -270,7 +278,7 @@ __device__ __forceinline__ T lagged(const T *U1, const T *U2, int idx)
 }
 
 // Pull-stream the Q populations of one species at (row, x): direction i
-// comes from element R.src[i] + (x, x - 1 or x + 1) of `in`, decoded against
+// comes from column x, x - 1 or x + 1 of the source row R.src[i] of `in`, decoded against
 // the source references `dec` for reduced-precision storage.
 template <int Q, typename T, typename S>
 __device__ __forceinline__ void pull(const S *__restrict__ in, const RowInfo &R, int x, int xm1,
@@ -280,9 +288,9 @@ __device__ __forceinline__ void pull(const S *__restrict__ in, const RowInfo &R,
     for (int i = 0; i < Q; ++i) {
         const int xs = ((R.xm >> i) & 1u) ? xm1 : (((R.xp >> i) & 1u) ? xp1 : x);
         if constexpr (Storage<S>::kRef)
-            g[i] = Storage<S>::load(in + R.src[i] + xs) * inv_scale + __ldg(dec + i);
+            g[i] = Storage<S>::load(src_row(in, R.src[i]) + xs) * inv_scale + __ldg(dec + i);
         else
-            g[i] = Storage<S>::load(in + R.src[i] + xs);
+            g[i] = Storage<S>::load(src_row(in, R.src[i]) + xs);
     }
 }
 
@@ -387,10 +395,11 @@ __device__ __noinline__ bool row_indices_ok(const StepArgs<T> &p, bool water, in
         site = kBadX;
     } else {
         const RowInfo &R = p.rows[cls][row];
-        const long long hi = (long long)(Q * p.n_rows[cls] - 1) * p.nxp;
+        const int unit = p.nxp / kRowAlign;
+        const long long hi = ((long long)Q * p.n_rows[cls] - 1) * unit;
         for (int i = 0; i < Q && !site; ++i) {
             const int v = R.src[i];
-            if (v < 0 || v > hi || v % p.nxp) site = kBadSource;
+            if (v < 0 || v > hi || v % unit) site = kBadSource;
         }
         if (!site && R.slot >= p.n_slots[cls]) site = kBadSlot;
         if (!site && (R.nface < 0 || R.nface > kMaxFaces)) site = kBadFaces;
@@ -552,7 +561,7 @@ __global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
             if (MODE == kModeField) {
                 T *f = p.field;
                 f[row * nxp + x] = c.drho;
-                for (int a = 0; a < 3; ++a) f[((a + 1) * p.n_rows[kFluid] + row) * nxp + x] = c.u[a];
+                for (int a = 0; a < 3; ++a) f[((size_t)(a + 1) * p.n_rows[kFluid] + row) * nxp + x] = c.u[a];
             } else {
                 const double ux = (double)c.u[0];
                 const double rho = (double)(p.rho0 + c.drho);
@@ -598,8 +607,8 @@ __global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
                 fe[row * nxp + x] = ce.drho;
                 fp[row * nxp + x] = cp.drho;
                 for (int a = 0; a < 3; ++a) {
-                    fe[((a + 1) * nrs + row) * nxp + x] = ce.u[a];
-                    fp[((a + 1) * nrs + row) * nxp + x] = cp.u[a];
+                    fe[((size_t)(a + 1) * nrs + row) * nxp + x] = ce.u[a];
+                    fp[((size_t)(a + 1) * nrs + row) * nxp + x] = cp.u[a];
                 }
             } else {
                 const double ue = (double)ce.u[0], up = (double)cp.u[0];
@@ -668,7 +677,7 @@ __global__ void __launch_bounds__(kBlockX) k_init(const StepArgs<T> p)
         Cell<T> c;
         c.drho = f[row * nxp + x];
         for (int a = 0; a < 3; ++a) {
-            c.u[a] = f[((a + 1) * nr + row) * nxp + x];
+            c.u[a] = f[((size_t)(a + 1) * nr + row) * nxp + x];
             c.F[a] = T(0);
         }
         // om = 1 and F = 0 make the collision produce exactly g^eq, whose
@@ -720,9 +729,9 @@ __device__ __forceinline__ T pull_one(const S *__restrict__ in, int src, int xs,
                                       int i, float inv_scale)
 {
     if constexpr (Storage<S>::kRef)
-        return Storage<S>::load(in + src + xs) * inv_scale + __ldg(dec + i);
+        return Storage<S>::load(src_row(in, src) + xs) * inv_scale + __ldg(dec + i);
     else
-        return Storage<S>::load(in + src + xs);
+        return Storage<S>::load(src_row(in, src) + xs);
 }
 
 template <int Q, typename T, typename S>
@@ -1070,7 +1079,7 @@ __global__ void k_ref_dec(const StepArgs<T> p, const float *enc0, const float *e
     const int row = s == 0 ? r : (s == 1 ? r - nrw : r - nrw - nrs);
     const int cls = s == 0 ? kFluid : kSolid;
     const int nr = s == 0 ? nrw : nrs;
-    const int q = p.rows[cls][row].src[i] / p.nxp;  // sdir * nr + srow
+    const int q = p.rows[cls][row].src[i] / (p.nxp / kRowAlign);  // sdir * nr + srow
     const int sdir = q / nr, srow = q - sdir * nr;
     const float *enc = s == 0 ? enc0 : (s == 1 ? enc1 : enc2);
     float *dec = s == 0 ? dec0 : (s == 1 ? dec1 : dec2);

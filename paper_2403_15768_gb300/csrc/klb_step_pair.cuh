@@ -154,7 +154,7 @@ template <typename S, bool REF>
 __device__ __forceinline__ float2 pull_dir(const S *__restrict__ in, int src, int shift, const Cols &X,
                                            float ref, float inv)
 {
-    const S *q = in + src;
+    const S *q = src_row(in, src);
     float2 v;
     if (shift == 0)
         v = Pair<S>::load2(q + X.x0);
@@ -333,7 +333,7 @@ __device__ __forceinline__ void store_pair(const float2 g[Q], S *__restrict__ ou
     for (int i = 0; i < Q; ++i) {
         float2 v = g[i];
         if constexpr (Storage<S>::kRef) v = fma2(v, b2(scale), b2(-__ldg(enc + i) * scale));
-        S *q = out + i * row_stride + base;
+        S *q = out + (long long)i * row_stride + base;
         if (both)
             Pair<S>::store2(q, v);
         else

@@ -165,3 +165,33 @@ def test_request_stream_recipe():
 
 def test_normal_build_has_no_index_checks():
     assert klb.load_library().klb_bounds_checked() == 0
+
+
+@pytest.mark.parametrize("change,msg", [
+    (dict(nx=0), ">= 1"),
+    (dict(ny=-2), ">= 1"),
+    (dict(radius=0), "radius"),
+    (dict(nx=65536, ny=2048, nz=2048, radius=900, shell=10), "32-bit"),
+])
+def test_degenerate_and_oversized_pipes_are_rejected(change, msg):
+    d = klb.desc_from_workload(inputs.PIPE_D3Q19_FP32.with_(**change))
+    assert klb.klb_lattice_bytes(d) == 0
+    with pytest.raises(klb.KLBError, match=msg):
+        klb.klb_lattice_info(d)
+
+
+def test_lattices_beyond_32_bit_class_buffers():
+    """Class buffers larger than 2^31 elements are admitted (row sources count
+    in 32-element units, plane strides are 64-bit): a 4096 x 512 x 512 pipe
+    (radius 240, shell 8) takes about 143 GB in FP32 and about half in FP16,
+    its water buffer holding 19 x 181k rows x 4096 = 1.4e10 elements.  What
+    stays 32-bit is one direction plane (rows x padded nx) and the box's cell
+    number: a plane of 2^31 elements or more is refused."""
+    w = inputs.PIPE_D3Q19_FP32.with_(nx=4096, ny=512, nz=512, radius=240, shell=8)
+    b32 = klb.klb_lattice_bytes(klb.desc_from_workload(w))
+    b16 = klb.klb_lattice_bytes(klb.desc_from_workload(w.with_(storage="fp16")))
+    assert 1.2e11 < b32 < 1.6e11 and 0.45 * b32 < b16 < 0.6 * b32
+    big_plane = w.with_(nx=3072, ny=1024, nz=1024, radius=480, storage="fp16")  # 723k rows x 3072
+    assert klb.klb_lattice_bytes(klb.desc_from_workload(big_plane)) == 0
+    with pytest.raises(klb.KLBError, match="row offsets"):
+        klb.klb_lattice_info(klb.desc_from_workload(big_plane))

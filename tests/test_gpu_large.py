@@ -1,0 +1,81 @@
+"""Lattices whose class buffers hold more than 2^31 elements (19 x 7232 rows
+x 16384 for the water of a 16384 x 128 x 128 nanotube, 9 x 32 rows x 2^23 for
+a D2Q9 slab): the row sources count in 32-element units and the plane
+strides are 64-bit, so every direction plane beyond the 32-bit range is
+addressed correctly.
+
+An x-invariant state stays x-invariant (the update of a cell sees only
+copies of its own row's values along x), so the long lattice started from
+rest must reproduce the 32-cell lattice of the same cross-section cell for
+cell: its per-slice observables equal the short lattice's and its totals are
+nx / 32 times them (to FP64 summation order; to storage precision for 16-bit
+storage, whose references round differently for different nx).  A wrong plane address would mix rows or directions and
+break both."""
+import math
+
+import pytest
+
+from paper_2403_15768_gb300 import inputs, klb
+
+pytestmark = pytest.mark.gpu
+
+PER_SLICE = ("flow_rate", "fit_A", "fit_B", "u_slip", "dudn_wall", "slip_length", "u_wallrow_mean",
+             "residual")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    klb.load_library()
+
+
+def _run(w, steps):
+    lat = klb.lattice_from_workload(w)
+    try:
+        lat.init_equilibrium()
+        lat.step(steps)
+        return lat.observables()
+    finally:
+        lat.close()
+
+
+def _close(a, b, rel):
+    if math.isnan(a) or math.isnan(b):
+        return math.isnan(a) and math.isnan(b)
+    return abs(a - b) <= rel * max(abs(a), abs(b)) + 1e-300
+
+
+@pytest.mark.parametrize("w,rel", [
+    (inputs.PIPE_D3Q19_FP32.with_(nx=16384), 1e-9),
+    # 16-bit storage: the row references are FP32 running sums over the
+    # row's 32-cell segments divided by nx, so their rounding (and with it
+    # the stored codes) depends on nx; the slices then agree to storage
+    # precision, not bit for bit.  A wrong plane address is an O(1) error.
+    (inputs.PIPE_D3Q19_FP32.with_(nx=16384, storage="fp16"), 1e-4),
+    (inputs.SLAB_D2Q9_FP64.with_(nx=1 << 23), 1e-9),
+], ids=["d3q19_fp32", "d3q19_fp16", "d2q9_fp64"])
+def test_long_lattice_reproduces_its_32_cell_slice(w, rel):
+    info = klb.klb_lattice_info(klb.desc_from_workload(w))
+    assert w.kind * info["species_cells"][0] >= 2 ** 31
+    steps = 40
+    big = _run(w, steps)
+    small = _run(w.with_(nx=32), steps)
+    r = w.nx / 32
+    assert big["nonfinite"] == 0 and small["nonfinite"] == 0
+    assert big["flow_rate"] > 0
+    # fit_B (the curvature of the early, nearly flat profile) and the slip
+    # quantities derived from it are small differences; under 16-bit storage
+    # they are compared through the profile they describe (fit_A, the wall-row
+    # mean, the flow rate) rather than one by one.
+    keys = PER_SLICE if w.storage != "fp16" else ("flow_rate", "fit_A", "u_wallrow_mean", "residual")
+    for k in keys:
+        assert _close(big[k], small[k], rel), (k, big[k], small[k])
+    for s in range(3):
+        assert _close(big["mean_u"][s], small["mean_u"][s], rel), ("mean_u", s)
+        assert _close(big["momentum"][s], r * small["momentum"][s], rel), ("momentum", s)
+        # mass deviations sum to nearly zero: compare per cell, at the
+        # rounding of the storage (2^-20 x 2^-11 per population for FP16)
+        eps = 1e-10 if w.storage == "fp16" else 3e-14
+        assert abs(big["mass"][s] - r * small["mass"][s]) <= eps * info["species_cells"][s], ("mass", s)
