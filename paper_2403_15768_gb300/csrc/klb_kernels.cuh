@@ -271,6 +271,15 @@ __device__ __forceinline__ const S *src_row(const S *in, int src)
     return in + (long long)src * kRowAlign;
 }
 
+// Programmatic dependent launch of consecutive steps.  A step kernel lets
+// the next step's grid be scheduled once all of its own blocks have started
+// (so the next step's blocks fill the SMs its last wave leaves idle and
+// load their row records), and every step waits for the previous kernel to
+// complete, its memory visible, before it reads or writes anything that
+// kernel reads or writes.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <typename T>
 __device__ __forceinline__ T lagged(const T *U1, const T *U2, int idx)
 {
@@ -908,6 +917,7 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
     const int4 q7 = __ldg(t4 + 7);          // flags, cs, pad, pad
     const uint32_t xp = (uint32_t)q5.x;
     const bool xbounce = (q7.x & kXBounce) != 0;
+    pdl_wait();  // populations, lagged velocities and references below
 
     if (water) {
         T g[Q], j[3];
@@ -1003,7 +1013,26 @@ __device__ __forceinline__ void step_cells_body(const StepArgs<T> &p, int b)
 template <int Q, typename T, typename S, bool ACC, bool NOISE = false>
 __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(const StepArgs<T> p)
 {
+    pdl_launch_dependents();
     step_cells_body<Q, T, S, ACC, NOISE>(p, blockIdx.x);
+}
+
+// Launch of a step kernel that may begin while the previous kernel of the
+// stream finishes (see pdl_wait).
+template <typename A>
+cudaError_t launch_step(void (*kernel)(A), int nblocks, int bx, cudaStream_t s, const A &a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3((unsigned)bx);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
 // Many lattices in one launch: the block finds its lattice as the number of
@@ -1095,20 +1124,17 @@ cudaError_t launch_q(const void *args, int mode, int nblocks, int bx, cudaStream
     const StepArgs<T> &a = *static_cast<const StepArgs<T> *>(args);
     switch (mode) {
     case kModeStep:
-        k_step<Q, T, S, false><<<nblocks, bx, 0, s>>>(a);
-        break;
+        return launch_step<StepArgs<T>>(k_step<Q, T, S, false>, nblocks, bx, s, a);
     case kModeStepAcc:
         if constexpr (Storage<S>::kRef)
-            k_step<Q, T, S, true><<<nblocks, bx, 0, s>>>(a);
+            return launch_step<StepArgs<T>>(k_step<Q, T, S, true>, nblocks, bx, s, a);
         else
             return cudaErrorInvalidValue;
-        break;
     case kModeStepNoise:
         if constexpr (!Storage<S>::kRef)
-            k_step<Q, T, S, false, true><<<nblocks, bx, 0, s>>>(a);
+            return launch_step<StepArgs<T>>(k_step<Q, T, S, false, true>, nblocks, bx, s, a);
         else
             return cudaErrorInvalidValue;
-        break;
     case kModeObserve:
         k_lattice<Q, T, S, kModeObserve><<<nblocks, bx, 0, s>>>(a);
         break;

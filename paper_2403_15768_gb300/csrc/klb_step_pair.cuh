@@ -424,6 +424,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     const bool xbounce = (q7.x & kXBounce) != 0;
 
     const int seg = ACC ? thread_segment<2>(p, water, row, x_first) : -1;
+    pdl_wait();  // populations, lagged velocities and references below
 
     if (water) {
         float2 g[Q], j[3];
