@@ -1018,7 +1018,7 @@ __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>())) k_step(con
 }
 
 // Launch of a step kernel that may begin while the previous kernel of the
-// stream finishes (see pdl_wait).
+// stream finishes (see pdl_wait); batched steps are launched the same way.
 template <typename A>
 cudaError_t launch_step(void (*kernel)(A), int nblocks, int bx, cudaStream_t s, const A &a)
 {
@@ -1044,6 +1044,7 @@ template <int Q, typename T, typename S, bool ACC>
 __global__ void __launch_bounds__(kBlockX, (step_min_blocks<T, S>()))
     k_step_batch(const StepArgs<T> *__restrict__ table, const int *__restrict__ prefix, int n)
 {
+    pdl_launch_dependents();
     __shared__ StepArgs<T> sp;
     __shared__ int s_lid;
     if (threadIdx.x == 0) s_lid = 0;
@@ -1161,15 +1162,22 @@ cudaError_t launch_batch_q(const void *table, const int *prefix, int n, int nblo
                            bool acc, cudaStream_t s)
 {
     const StepArgs<T> *t = static_cast<const StepArgs<T> *>(table);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3((unsigned)bx);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (acc) {
         if constexpr (Storage<S>::kRef)
-            k_step_batch<Q, T, S, true><<<nblocks, bx, 0, s>>>(t, prefix, n);
+            return cudaLaunchKernelEx(&cfg, k_step_batch<Q, T, S, true>, t, prefix, n);
         else
             return cudaErrorInvalidValue;
-    } else {
-        k_step_batch<Q, T, S, false><<<nblocks, bx, 0, s>>>(t, prefix, n);
     }
-    return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_step_batch<Q, T, S, false>, t, prefix, n);
 }
 
 template <int Q, typename T>
