@@ -38,35 +38,39 @@ cudaError_t launch_ref(int Q, int storage, const void *args, float *const enc[3]
 }
 
 // Deterministic final reduction of the per-block partial sums: block k
-// reduces sum k (strided per-thread sums in a fixed order, then a tree).
-__global__ void __launch_bounds__(256) k_finalize(const double *__restrict__ partials, int nblocks,
-                                                  double *__restrict__ sums)
+// reduces sum k.  Each thread keeps four accumulators over interleaved
+// partials (four independent loads in flight), combines them in a fixed
+// order, then the block reduces the threads' values in a fixed tree.
+constexpr int kFinalizeThreads = 1024;
+
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const double *__restrict__ partials, int nblocks,
+                                                               double *__restrict__ sums)
 {
-    __shared__ double red[256];
-    {
-        const int k = blockIdx.x;
-        const bool is_max = k == kSumResidual;
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-            const double q = partials[(size_t)b * kNumSums + k];
-            v = is_max ? fmax(v, q) : v + q;
+    __shared__ double red[kFinalizeThreads];
+    const int k = blockIdx.x;
+    const bool is_max = k == kSumResidual;
+    auto op = [is_max](double a, double b) { return is_max ? fmax(a, b) : a + b; };
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    const int step = 4 * kFinalizeThreads;
+    for (int b0 = threadIdx.x; b0 < nblocks; b0 += step) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int b = b0 + u * kFinalizeThreads;
+            if (b < nblocks) v[u] = op(v[u], partials[(size_t)b * kNumSums + k]);
         }
-        red[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w)
-                red[threadIdx.x] = is_max ? fmax(red[threadIdx.x], red[threadIdx.x + w])
-                                          : red[threadIdx.x] + red[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) sums[k] = red[0];
+    }
+    red[threadIdx.x] = op(op(v[0], v[1]), op(v[2], v[3]));
+    __syncthreads();
+    for (int w = kFinalizeThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] = op(red[threadIdx.x], red[threadIdx.x + w]);
         __syncthreads();
     }
+    if (threadIdx.x == 0) sums[k] = red[0];
 }
 
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s)
 {
-    k_finalize<<<kNumSums, 256, 0, s>>>(partials, nblocks, sums);
+    k_finalize<<<kNumSums, kFinalizeThreads, 0, s>>>(partials, nblocks, sums);
     return cudaGetLastError();
 }
 
