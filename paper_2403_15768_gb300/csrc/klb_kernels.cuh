@@ -534,7 +534,7 @@ __device__ __forceinline__ bool finite3(const Cell<T> &c)
 // Observation and field passes.
 
 template <int Q, typename T, typename S, int MODE>
-__global__ void __launch_bounds__(kBlockX) k_lattice(const StepArgs<T> p)
+__global__ void __launch_bounds__(kBlockX, (sizeof(T) == 4 ? 8 : 1)) k_lattice(const StepArgs<T> p)
 {
     const int b = blockIdx.x;
     const bool water = b < p.nbw;
