@@ -1,0 +1,126 @@
+"""Parity at the full sizes the benchmark runs: the 768 x 192 x 192 nanotube
+with FP16 and BF16 storage, and the 96-channel design sweep stepped as one
+batch.
+
+Lattices started from rest stay exactly x-invariant (every x plane sees
+copies of its own row's values), so every x plane must equal the oracle run
+on the same cross-section with one x plane; the oracle then finishes in
+seconds at any nx.  Sampled x planes are checked for x-invariance, plane 0
+against the oracle.
+
+Tolerances: the errors measured on GB300 with a margin of about 2x, as for
+the other parity tests.  Nanotube 768 x 192 x 192 after 5000 steps, rel-L2
+of the velocity fields against the oracle: FP32 3.0e-5, FP16 2.7e-5, BF16
+1.3e-4 (water; electrons and phonons below 7e-6), 16-bit against the FP32
+GPU run 4.5e-6 (FP16) and 1.1e-4 (BF16); flow rate within 1e-4, slip length
+within 0.1% (FP32) and 1% (16-bit).  Sweep after 300 steps from rest, fields
+and flow rates of six members: FP32 at most 2.9e-6, FP16 at most 6.0e-4 (a
+narrow slab whose flow is still small, so that the 16-bit rounding is a
+larger fraction of it; the paper's 1% bar for 16-bit storage is far off).
+"""
+import numpy as np
+import pytest
+
+from klb_testutil import make_oracle, rel_l2, species_masks
+from oracle import observables_from_fields
+from paper_2403_15768_gb300 import inputs, klb
+
+pytestmark = pytest.mark.gpu
+
+LARGE_STEPS = 5000
+SWEEP_STEPS = 300
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    klb.load_library()
+
+
+def _planes(u, nx):
+    """The x planes checked for x-invariance."""
+    return sorted({0, 1, nx // 2, nx - 1})
+
+
+def _oracle_plane(w, steps):
+    o = make_oracle(w, nx=1)
+    o.init_equilibrium()
+    o.step(steps)
+    f = o.observe()
+    return o.geo, f, observables_from_fields(o.geo, 1, w.rho0, f)
+
+
+def _gpu_plane(lat, nx):
+    """Velocity fields of x plane 0, after checking that the sampled planes
+    are identical to it."""
+    _, u = lat.get_field()
+    for x in _planes(u, nx):
+        assert np.array_equal(u[..., x], u[..., 0]), x
+    return np.ascontiguousarray(u[..., :1])
+
+
+_LARGE = {}
+
+
+def _large(storage):
+    w = inputs.PIPE_D3Q19_LARGE
+    if "oracle" not in _LARGE:
+        _LARGE["oracle"] = _oracle_plane(w, LARGE_STEPS)
+    if storage not in _LARGE:
+        lat = klb.lattice_from_workload(w.with_(storage=storage))
+        lat.step(LARGE_STEPS)
+        _LARGE[storage] = (_gpu_plane(lat, w.nx), lat.observables())
+        lat.close()
+    return _LARGE["oracle"], _LARGE[storage]
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 6e-5), ("bf16", 3e-4)])
+def test_large_nanotube_16bit_against_oracle_and_fp32(storage, tol):
+    (geo, f, ob_o), (u16, ob16) = _large(storage)
+    _, (u32, ob32) = _large("fp32")
+    m = species_masks(geo, 1)
+    e32 = [rel_l2(u32[s][:, m[s]], f["u"][s][:, m[s]]) for s in range(3)]
+    e16 = [rel_l2(u16[s][:, m[s]], f["u"][s][:, m[s]]) for s in range(3)]
+    d16 = [rel_l2(u16[s][:, m[s]], u32[s][:, m[s]]) for s in range(3)]
+    report = {"fp32": e32, storage: e16, "vs fp32": d16}
+    print(report)
+    assert max(e32) <= 6e-5 and max(e16) <= tol and max(d16) <= tol, report
+    assert ob32["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
+    assert ob16["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-2)
+    for ob in (ob32, ob16):
+        assert ob["flow_rate"] == pytest.approx(ob_o["flow_rate"], rel=1e-4)
+        assert ob["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 6e-6), ("fp16", 1.5e-3)])
+def test_full_sweep_batch_sampled_members_against_oracle(storage, tol):
+    """All 96 channels of the sweep in one batch (the benchmark's lattices),
+    from rest; six members spanning the size range checked plane by plane."""
+    import torch
+
+    ws = inputs.channel_sweep(96, 0, storage=storage)
+    lats = [klb.lattice_from_workload(w) for w in ws]
+    b = klb.Batch(lats)
+    b.step(SWEEP_STEPS)
+    order = np.argsort([lat.species_cells(0) + 2 * lat.species_cells(1) for lat in lats], kind="stable")
+    sample = [int(order[k]) for k in (0, 19, 38, 57, 76, 95)]
+    errs = {}
+    for k in sample:
+        w, lat = ws[k], lats[k]
+        geo, f, ob_o = _oracle_plane(w, SWEEP_STEPS)
+        u = _gpu_plane(lat, w.nx)
+        m = species_masks(geo, 1)
+        errs[k] = [rel_l2(u[s][:, m[s]], f["u"][s][:, m[s]]) for s in range(3)]
+        ob = lat.observables()
+        errs[k].append(abs(ob["flow_rate"] / ob_o["flow_rate"] - 1.0))
+        assert ob["nonfinite"] == 0
+    b.close()
+    for lat in lats:
+        lat.close()
+    torch.cuda.empty_cache()
+    report = {ws[k].name: ["%.2e" % e for e in v] for k, v in errs.items()}
+    print(report)
+    for k, v in errs.items():
+        assert max(v[:3]) <= tol and v[3] <= tol, report
