@@ -1,6 +1,6 @@
 """Parity at the full sizes the benchmark runs: the 768 x 192 x 192 nanotube
-with FP16 and BF16 storage, and the 96-channel design sweep stepped as one
-batch.
+with FP16 and BF16 storage, the 96-channel design sweep stepped as one
+batch, and the serving stream's requests (up to 512 x 128 x 128 cells).
 
 Lattices started from rest stay exactly x-invariant (every x plane sees
 copies of its own row's values), so every x plane must equal the oracle run
@@ -16,7 +16,8 @@ GPU run 4.5e-6 (FP16) and 1.1e-4 (BF16); flow rate within 1e-4, slip length
 within 0.1% (FP32) and 1% (16-bit).  Sweep after 300 steps from rest, fields
 and flow rates of six members: FP32 at most 2.9e-6, FP16 at most 6.0e-4 (a
 narrow slab whose flow is still small, so that the 16-bit rounding is a
-larger fraction of it; the paper's 1% bar for 16-bit storage is far off).
+larger fraction of it; the paper's 1% bar for 16-bit storage is far off);
+the served requests, retired at the same step count, at the sweep's bounds.
 """
 import numpy as np
 import pytest
@@ -124,3 +125,31 @@ def test_full_sweep_batch_sampled_members_against_oracle(storage, tol):
     print(report)
     for k, v in errs.items():
         assert max(v[:3]) <= tol and v[3] <= tol, report
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 6e-6), ("fp16", 1.5e-3)])
+def test_serving_stream_at_full_size_against_oracle(storage, tol):
+    """Twelve requests of the benchmark's Poisson stream (seed 0, up to
+    512 x 128 x 128 cells), all resident in one server and retired at a
+    300-step limit: each result's flow rate against the oracle plane after
+    the same number of steps."""
+    reqs = inputs.request_stream(12, rate=50.0, seed=0, storage=storage)
+    need = sum(klb.klb_lattice_bytes(klb.desc_from_workload(r.w)) for r in reqs)
+    arena = klb.klb_server_table_bytes(klb.STORAGE[storage], 16) + need + 256 * len(reqs)
+    srv = klb.Server(arena, storage=storage, check_every=100, max_resident=16)
+    for r in reqs:
+        srv.submit(klb.desc_from_workload(r.w), r.w.couplings, 1e-300, SWEEP_STEPS, r.rid)
+    out = {}
+    while len(out) < len(reqs):
+        srv.tick()
+        for res in srv.poll():
+            out[res["id"]] = res
+    srv.close()
+    errs = {}
+    for r in reqs:
+        res = out[r.rid]
+        assert res["status"] == 5 and res["steps"] == SWEEP_STEPS, res  # KLB_ETIMEOUT: the step limit
+        _, _, ob_o = _oracle_plane(r.w, res["steps"])
+        errs[r.w.name] = abs(res["obs"]["flow_rate"] / ob_o["flow_rate"] - 1.0)
+        assert res["obs"]["nonfinite"] == 0
+    assert max(errs.values()) <= tol, errs
