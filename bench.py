@@ -339,7 +339,7 @@ def run_sweep(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     storage = args.workload.split("_", 1)[1]
-    ws = inputs.channel_sweep(96, seed=rank, storage=storage)
+    ws = inputs.channel_sweep(96, seed=rank, storage=storage, scale=args.scale)
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         lats = [klb.lattice_from_workload(w, device=dev, stream=stream) for w in ws]
@@ -402,7 +402,8 @@ def run_sweep(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"design sweep of 96 D3Q19 channels (seed = rank), {storage}",
+        "config": {"workload": f"design sweep of 96 D3Q19 channels (seed = rank), {storage}"
+                               + (f", lengths x{args.scale:g}" if args.scale != 1.0 else ""),
                    "storage": storage, "channels": len(lats), "active_sites": sites,
                    "lattice_steps_per_step": SWEEP_STEPS, "block_width": width,
                    "blocks_per_launch": batch.blocks, "parallelism": f"replicas x{world}",
@@ -544,6 +545,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="nanotube", choices=WORKLOADS)
     ap.add_argument("--rate", type=float, default=50.0, help="serving: requests per second")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="sweeps: every channel length times this factor (1 = the 96-channel sweep)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 48 if args.workload.startswith("serving_") else (
