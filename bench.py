@@ -8,11 +8,14 @@ the FP64 observation pass (flow rate, slip length, masses, momenta,
 residual).
 
 Other workloads (--workload):
+  nanotube_noise  the default nanotube with thermal fluctuations of the
+      water (kT = 1e-5, Philox-keyed noise after every collision).
   nanotube_large_{fp32,fp16,bf16}  the nanotube scaled to 768 x 192 x 192
       (radius 72, shell 9), populations in FP32 or as 16-bit differences
       from per-row references; same step as the default.
   sweep_{fp32,fp16}  96 seeded channels of a design sweep in one batch (one
-      launch per lattice step, graph replay, autotuned block width); one
+      launch per lattice step, graph replay, autotuned block width; --scale
+      multiplies every channel length); one
       benchmark step = 384 lattice steps of every channel + the observation
       pass of every channel.
   serving_{fp32,fp16}  a seeded Poisson stream of design-sweep requests
@@ -210,6 +213,7 @@ def run_reference(args):
 
 
 STORAGE_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
+NOISE_KT = 1e-5  # thermal energy of the nanotube_noise workload (lattice units)
 
 
 def run(args):
@@ -226,13 +230,16 @@ def run(args):
     rank, local, world, dist = _dist_setup(args.gpus)
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    if args.workload == "nanotube":
+    kT = NOISE_KT if args.workload == "nanotube_noise" else 0.0
+    if args.workload in ("nanotube", "nanotube_noise"):
         w = inputs.PIPE_D3Q19_FP32
     else:
         w = inputs.PIPE_D3Q19_LARGE.with_(storage=args.workload.rsplit("_", 1)[1])
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         lat = klb.lattice_from_workload(w, device=dev, stream=stream)
+        if kT > 0.0:
+            lat.set_fluctuations(kT, seed=rank)
     sites = lat.active_sites()
     species_cells = sum(lat.species_cells(s) for s in range(3))
     bytes_per_launch = species_cells * 2 * 19 * STORAGE_BYTES[w.storage]  # read + write of every population
@@ -301,11 +308,12 @@ def run(args):
                    "lattice_steps_per_step": LATTICE_STEPS_PER_STEP,
                    "observables_per_step": 1, "parallelism": f"replicas x{world}",
                    "l2": f"working set {lat.nbytes / 1e9:.2f} GB per GPU > 129 MB L2, no flush needed",
-                   "couplings": list(w.couplings)},
+                   "couplings": list(w.couplings), **({"kT": kT} if kT > 0 else {})},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": _ncu_traffic() if args.workload == "nanotube" else None,
-                     "kernel": f"k_step<19,float,{w.storage}>", "peak_source": peak_kind,
+                     "kernel": f"k_step<19,float,{w.storage}{',noise' if kT > 0 else ''}>",
+                     "peak_source": peak_kind,
                      "bytes_per_launch": bytes_per_launch, "launch_ms": step_kernel_ms},
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": 40,
                 "d2h_bytes_per_step": 144},
@@ -533,7 +541,7 @@ def run_design_map(args):
         dist.destroy_process_group()
 
 
-WORKLOADS = ["nanotube", "nanotube_large_fp32", "nanotube_large_fp16", "nanotube_large_bf16",
+WORKLOADS = ["nanotube", "nanotube_noise", "nanotube_large_fp32", "nanotube_large_fp16", "nanotube_large_bf16",
              "sweep_fp32", "sweep_fp16", "serving_fp32", "serving_fp16", "design_map"]
 
 

@@ -850,23 +850,25 @@ __device__ __forceinline__ void weighted_normals(uint32_t cell, uint32_t slo, ui
 }
 
 // Calls add(i, xi_i) with the noise of one water cell (see above); the
-// normals are drawn twice (sums, then terms) rather than held.
+// normals are drawn once and held for the projection.
 template <int Q, typename T, typename F>
 __device__ __forceinline__ void thermal_noise(const StepArgs<T> &p, uint32_t cell, F add)
 {
-    T S0 = T(0), S1[3] = {T(0), T(0), T(0)};
-    weighted_normals<Q, T>(cell, p.step_lo, p.step_hi, p.key[0], p.key[1], [&](int i, T a) {
-        S0 += a;
-        if (cx<Q>(i)) S1[0] += T(cx<Q>(i)) * a;
-        if (cy<Q>(i)) S1[1] += T(cy<Q>(i)) * a;
-        if (cz<Q>(i)) S1[2] += T(cz<Q>(i)) * a;
+    T S0 = T(0), S1[3] = {T(0), T(0), T(0)}, a[Q];
+    weighted_normals<Q, T>(cell, p.step_lo, p.step_hi, p.key[0], p.key[1], [&](int i, T v) {
+        a[i] = v;
+        S0 += v;
+        if (cx<Q>(i)) S1[0] += T(cx<Q>(i)) * v;
+        if (cy<Q>(i)) S1[1] += T(cy<Q>(i)) * v;
+        if (cz<Q>(i)) S1[2] += T(cz<Q>(i)) * v;
     });
     const T A = p.noise_amp;
-    weighted_normals<Q, T>(cell, p.step_lo, p.step_hi, p.key[0], p.key[1], [&](int i, T a) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
         const T w = T(wt<Q>(i));
         const T cS = T(cx<Q>(i)) * S1[0] + T(cy<Q>(i)) * S1[1] + T(cz<Q>(i)) * S1[2];
-        add(i, A * (a - w * S0 - T(3) * w * cS));
-    });
+        add(i, A * (a[i] - w * S0 - T(3) * w * cS));
+    }
 }
 
 template <typename T, typename S>
