@@ -800,16 +800,20 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // Two normals from two generator words (Box-Muller).  FP32: u = r 2^-32 +
-// 2^-33 (exact for small r, where the logarithm is sensitive).
+// 2^-33 (exact for small r, where the logarithm is sensitive); the hardware
+// logarithm and sine/cosine (relative error near 1e-6, far below what the
+// statistics of the noise can resolve), the angle taken as
+// 2 pi (u2 - 1/2) in [-pi, pi), where the fast sine/cosine are accurate,
+// and the half turn undone by negating both.
 __device__ __forceinline__ void box_muller(uint32_t r1, uint32_t r2, float &z1, float &z2)
 {
     const float u1 = fmaf(__uint2float_rn(r1), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float u2 = fmaf(__uint2float_rn(r2), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float R = sqrtf(-2.f * logf(u1));
+    const float R = sqrtf(-2.f * __logf(u1));
     float sn, cs;
-    sincospif(2.f * u2, &sn, &cs);
-    z1 = R * cs;
-    z2 = R * sn;
+    __sincosf(6.2831853071795865f * (u2 - 0.5f), &sn, &cs);
+    z1 = -R * cs;
+    z2 = -R * sn;
 }
 __device__ __forceinline__ void box_muller(uint32_t r1, uint32_t r2, double &z1, double &z2)
 {
