@@ -38,3 +38,22 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["metric"] == "MLUPS" and line["value"] > 0
     assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_profile_traffic_follows_the_kernel_sources(monkeypatch):
+    """The benchmark reports the committed ncu traffic of the step kernel only
+    for the kernel sources it was taken on, and then within a few percent of
+    the algorithmic bytes (no re-reads); after a source change it reports
+    none."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    txt = open(bench.PROFILE).read()
+    assert "kernel_source_sha256_16:" in txt and "dram_bytes_per_launch:" in txt
+    algorithmic = 5_693_440 * 2 * 19 * 4
+    t = bench._ncu_traffic()
+    assert t is None or 0.95 * algorithmic < t < 1.05 * algorithmic
+    monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "0" * 16)
+    assert bench._ncu_traffic() is None
