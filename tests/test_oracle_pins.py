@@ -294,6 +294,34 @@ def test_free_acceleration(Q, geo):
         assert np.abs(u[1:][:, fluid]).max() < 1e-18
 
 
+@pytest.mark.parametrize("Q,geo", [
+    (9, cross_section("slab", 40, 1, width=32, shell=4)),
+    (19, cross_section("pipe", 26, 26, radius=9, shell=3)),
+])
+def test_free_acceleration_observables(Q, geo):
+    """The observables of the uniformly accelerating fluid, each from its
+    definition: flow rate (1/nx) sum u_x = N_fluid,slice G (n + 1/2),
+    wall-row and water means G (n + 1/2), electron and phonon means 0,
+    water momentum rho0 N_fluid G (n + 1/2), zero mass deviations, residual
+    max |u(n) - u(n-1)| = G, no non-finite value."""
+    G, nx, n = 1e-5, 3, 20
+    o = Oracle(Q, nx, geo, tau=(0.8, 0.6, 1.0), G=(G, 0, 0))
+    o.init_equilibrium()
+    o.step(n)
+    ob = o.observables()
+    n_cs = int((geo.cs_type == T_FLUID).sum())
+    u = G * (n + 0.5)
+    tol = 1e-12
+    assert ob["flow_rate"] == pytest.approx(n_cs * u, rel=tol)
+    assert ob["u_wallrow_mean"] == pytest.approx(u, rel=tol)
+    assert ob["mean_u"][0] == pytest.approx(u, rel=tol)
+    assert abs(ob["mean_u"][1]) < 1e-18 and abs(ob["mean_u"][2]) < 1e-18
+    assert ob["momentum"][0] == pytest.approx(n_cs * nx * u, rel=tol)
+    assert max(abs(m) for m in ob["mass"]) < 1e-15
+    assert ob["residual"] == pytest.approx(G, rel=1e-9)
+    assert ob["nonfinite"] == 0 and ob["step"] == n
+
+
 def test_electron_phonon_crank_nicolson():
     """One uniform solid: delta = u_e - u_p decays by (1 - k/2)/(1 + k/2) per
     step, k = gamma_ep (1/rho_e + 1/rho_p); a phonon sink alone decays u_p by
