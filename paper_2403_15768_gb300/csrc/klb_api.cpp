@@ -1171,9 +1171,13 @@ klb_status klb_batch_autotune(klb_batch *B, int steps_per_candidate, int *width)
     if (!in_phase(B))
         return bfail(B, KLB_ESTATE, "a member was stepped outside the batch; form the batch again");
     KLB_BCUDA(B, cudaStreamSynchronize(B->user));
-    cudaEvent_t t0, t1;
-    KLB_BCUDA(B, cudaEventCreate(&t0));
-    KLB_BCUDA(B, cudaEventCreate(&t1));
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&t0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&t1);
+    if (ce != cudaSuccess) {
+        if (t0) cudaEventDestroy(t0);
+        return bfail(B, KLB_ECUDA, std::string("autotune events: ") + cudaGetErrorString(ce));
+    }
     const int cand[3] = {32, 64, 128};
     int best = B->width;
     float best_ms = 1e30f;
@@ -1183,12 +1187,16 @@ klb_status klb_batch_autotune(klb_batch *B, int steps_per_candidate, int *width)
         if (st != KLB_OK) break;
         st = run_steps(B, 1, false);  // warm-up
         if (st != KLB_OK) break;
-        cudaEventRecord(t0, B->stream);
+        if (cudaEventRecord(t0, B->stream) != cudaSuccess) {
+            st = bfail(B, KLB_ECUDA, "autotune timing");
+            break;
+        }
         st = run_steps(B, steps_per_candidate, false);
-        cudaEventRecord(t1, B->stream);
-        if (cudaEventSynchronize(t1) != cudaSuccess) st = bfail(B, KLB_ECUDA, "autotune timing");
+        if (st != KLB_OK) break;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, t0, t1);
+        if (cudaEventRecord(t1, B->stream) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess)
+            st = bfail(B, KLB_ECUDA, "autotune timing");
         if (st == KLB_OK && ms < best_ms) {
             best_ms = ms;
             best = cand[c];
