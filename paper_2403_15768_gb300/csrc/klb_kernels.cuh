@@ -884,8 +884,11 @@ constexpr int step_min_blocks()
 template <int Q, typename T, typename S, bool ACC, bool NOISE = false>
 __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
 {
-    const bool water = b < p.snbw;
-    const int bb = water ? b : b - p.snbw;
+    // solid blocks (two species each, the heavier work) first, so that the
+    // grid's last wave holds the lighter water blocks
+    const int nsb = p.n_rows[kSolid] * p.snchunk_s;
+    const bool water = b >= nsb;
+    const int bb = water ? b - nsb : b;
     const int nch = water ? p.snchunk_w : p.snchunk_s;
     int row = bb / nch;
     int x = (bb - row * nch) * blockDim.x + threadIdx.x;

@@ -381,8 +381,11 @@ __device__ __forceinline__ int thread_segment(const StepArgs<float> &p, bool wat
 template <int Q, typename S, bool ACC, bool NOISE = false>
 __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
 {
-    const bool water = b < p.snbw;
-    const int bb = water ? b : b - p.snbw;
+    // solid blocks (two species each, the heavier work) first, so that the
+    // grid's last wave holds the lighter water blocks
+    const int nsb = p.n_rows[kSolid] * p.snchunk_s;
+    const bool water = b >= nsb;
+    const int bb = water ? b - nsb : b;
     const int nch = water ? p.snchunk_w : p.snchunk_s;
     int row = bb / nch;
     const int xt = (bb - row * nch) * blockDim.x + threadIdx.x;
