@@ -195,3 +195,43 @@ def test_lattices_beyond_32_bit_class_buffers():
     assert klb.klb_lattice_bytes(klb.desc_from_workload(big_plane)) == 0
     with pytest.raises(klb.KLBError, match="row offsets"):
         klb.klb_lattice_info(klb.desc_from_workload(big_plane))
+
+
+def test_serving_summary_statistics():
+    """Latency = finish - arrival (queueing included), wait = admission -
+    arrival, aggregate rate = site updates over the span from the first
+    arrival to the last finish; unfinished requests are counted apart."""
+    from paper_2403_15768_gb300 import serving
+
+    def res(rid, arrival, admitted, finished, sites, steps, status=0):
+        return {"id": rid, "arrival": arrival, "admitted": admitted, "finished": finished,
+                "sites": sites, "steps": steps, "status": status}
+
+    rs = [res(k, 0.1 * k, 0.1 * k + 0.01 * k, 0.1 * k + 1.0 + k, 1000, 100 * (k + 1)) for k in range(10)]
+    rs[3]["status"] = 5
+    s = serving.summarise({"results": rs + [None]})
+    lat = np.array([1.0 + k for k in range(10)])
+    wait = np.array([0.01 * k for k in range(10)])
+    assert s["finished"] == 10 and s["submitted"] == 11
+    assert s["p50_s"] == pytest.approx(np.percentile(lat, 50)) and s["p99_s"] == pytest.approx(np.percentile(lat, 99))
+    assert s["wait_p99_s"] == pytest.approx(np.percentile(wait, 99))
+    span = (0.9 + 1.0 + 9) - 0.0
+    assert s["makespan_s"] == pytest.approx(span)
+    assert s["mlups"] == pytest.approx(sum(1000 * 100 * (k + 1) for k in range(10)) / span / 1e6)
+    assert s["status"] == {"KLB_OK": 9, "KLB_ETIMEOUT": 1}
+    assert serving.summarise({"results": [None]}) == {"finished": 0}
+
+
+def test_design_grid_recipe():
+    """One pipe per (radius, g_we): box side 2 (radius + shell) + 2, the
+    fixed couplings, net wall friction for a steady state, and every point a
+    valid lattice."""
+    ws = inputs.design_grid([6, 8, 12], [-0.02, 0.0, 0.05], nx=8, shell=3)
+    assert len(ws) == 9
+    for w in ws:
+        assert w.geom == "pipe" and w.nx == 8 and w.ny == w.nz == 2 * (w.radius + w.shell) + 2
+        g_we, g_wp = w.couplings[0], w.couplings[1]
+        assert g_we + g_wp > 0  # a steady state exists
+        assert klb.klb_lattice_bytes(klb.desc_from_workload(w)) > 0
+    assert sorted({w.radius for w in ws}) == [6, 8, 12]
+    assert sorted({w.couplings[0] for w in ws}) == [-0.02, 0.0, 0.05]
