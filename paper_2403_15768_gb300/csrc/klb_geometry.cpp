@@ -68,7 +68,7 @@ struct CrossSection {
         }
         return true;
     }
-    int type(int y, int z) const { return wrap(y, z) ? (*t)[y + ny * z] : kVoid; }
+    int type(int y, int z) const { return wrap(y, z) ? (int)(*t)[y + ny * z] : (int)kVoid; }
     int index(int y, int z) const
     {
         wrap(y, z);
