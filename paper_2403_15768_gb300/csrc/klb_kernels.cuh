@@ -13,8 +13,10 @@
 // nxp elements (x fastest, rows padded to 32 elements), so every load and
 // store of a warp is a contiguous run of x.  A block covers up to 128
 // consecutive x of one row; the row table (sources, x shifts, interface
-// partners) is block-uniform.  Water blocks come first in the grid, then the
-// solid blocks, each of which updates the electrons and phonons of its row.
+// partners) is block-uniform.  A solid block updates the electrons and
+// phonons of its row together; the step grid puts the solid blocks first
+// (the heavier work, so that its last wave holds water blocks), the
+// observation, field and initialisation grids the water blocks first.
 //
 // Template parameters: Q (9 or 19), T the arithmetic type (double or float)
 // and S the storage type of the populations (T itself, or __half /
