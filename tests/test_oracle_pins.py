@@ -604,6 +604,21 @@ def test_steady_pipe_closed_form():
     assert abs(obs["fit_B"] + G / (4 * nu)) < 0.02 * G / (4 * nu)
     _, Q = slip_poiseuille_pipe(G, 1.0, tau, geo.d_wall, obs["slip_length"])
     assert abs(obs["flow_rate"] - Q) < 0.02 * Q
+    # P7 for the pipe: at steady state the drive on the water of a slice
+    # equals the interface friction summed over its fluid/solid faces
+    # (specular faces carry no momentum), exactly.
+    u = o.observe()["u"]
+    uw, ue, up = u[0][0][..., 0], u[1][0][..., 0], u[2][0][..., 0]
+    t = geo.cs_type
+    g_we, g_wp = 0.05, 0.02
+    friction = 0.0
+    for z, y in zip(*np.nonzero(t == T_FLUID)):
+        for dz, dy in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+            zz, yy = z + dz, y + dy
+            if 0 <= zz < geo.nz and 0 <= yy < geo.ny and t[zz, yy] == T_SOLID:
+                friction += g_we * (uw[z, y] - ue[zz, yy]) + g_wp * (uw[z, y] - up[zz, yy])
+    drive = G * int((t == T_FLUID).sum())
+    assert abs(friction - drive) < 1e-9 * drive
 
 
 # ---------------------------------------------------------------------------
