@@ -143,7 +143,12 @@ typedef struct {
 } klb_obs;
 
 /* Device bytes klb_create_lattice needs for this description (0 if the
- * description is invalid).  Pure host computation. */
+ * description is invalid).  Pure host computation.  Index widths bound a
+ * lattice: the box's cell count nx*ny*nz below 2^32, one direction plane
+ * of a species class (its rows x nx padded to 32) below 2^31 elements, and
+ * the interface velocities of a class (3 or 6 x its interface rows x padded
+ * nx) below 2^31; a class's whole population buffer may exceed 2^31
+ * elements (a single lattice can fill the device). */
 size_t klb_lattice_bytes(const klb_desc *desc);
 
 /* Sizes of a lattice, from the description alone (host computation):
@@ -177,7 +182,8 @@ klb_status klb_lattice_info(const klb_desc *desc, klb_info *info);
  * all later work of the handle is enqueued.  `dev_buf` must outlive the
  * handle.  Synchronises the stream once.  Returns KLB_EINVAL for a bad
  * description (tau <= 1/2, rho0 <= 0, non-finite values, nz != 1 for D2Q9, a
- * shell of 0, an empty species, a box too large for 32-bit row offsets),
+ * shell of 0, an empty species, a box beyond the index widths of
+ * klb_lattice_bytes),
  * KLB_ENOMEM if `bytes` is too small.  Couplings start at zero.
  */
 klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
