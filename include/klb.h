@@ -143,7 +143,9 @@ typedef struct {
 } klb_obs;
 
 /* Device bytes klb_create_lattice needs for this description (0 if the
- * description is invalid).  Pure host computation.  Index widths bound a
+ * description is invalid): the three population sets of Sec. 4 (two
+ * buffers each), the lagged interface velocities of Eq. 27 and small
+ * tables.  Pure host computation.  Index widths bound a
  * lattice: the box's cell count nx*ny*nz below 2^32, one direction plane
  * of a species class (its rows x nx padded to 32) below 2^31 elements, and
  * the interface velocities of a class (3 or 6 x its interface rows x padded
@@ -151,7 +153,8 @@ typedef struct {
  * elements (a single lattice can fill the device). */
 size_t klb_lattice_bytes(const klb_desc *desc);
 
-/* Sizes of a lattice, from the description alone (host computation):
+/* Sizes of a lattice, from the description alone (host computation; the
+ * geometry rules of Sec. 4.2, the nanotube of Sec. 5.1):
  *   fluid_cs / solid_cs     fluid / solid cells of one cross-section;
  *   species_cells[s]        cells carrying species s (whole box);
  *   active_sites            fluid + solid cells (whole box);
@@ -175,7 +178,8 @@ typedef struct {
 klb_status klb_lattice_info(const klb_desc *desc, klb_info *info);
 
 /*
- * Build the lattice in the caller's device buffer `dev_buf` (at least
+ * Build the lattice of Sec. 4 (water on the fluid cells, electrons and
+ * phonons on the solid cells, Sec. 3.1-3.4) in the caller's device buffer `dev_buf` (at least
  * klb_lattice_bytes(desc) bytes, 256-byte aligned, on the current device)
  * and start from rest: every population deviation and lagged velocity is 0.
  * `cuda_stream` is a cudaStream_t (NULL: the legacy default stream) on which
@@ -189,7 +193,7 @@ klb_status klb_lattice_info(const klb_desc *desc, klb_info *info);
 klb_status klb_create_lattice(const klb_desc *desc, void *dev_buf, size_t bytes,
                               void *cuda_stream, klb_lattice **out);
 
-/* Set the friction coefficients.  KLB_EINVAL for non-finite values or for
+/* Set the friction coefficients (Eq. 27; Eqs. 5, 11-16).  KLB_EINVAL for non-finite values or for
  * couplings beyond the stability bound of the lagged interface exchange:
  * max over cells of (sum over its faces of |g| of its species pairs) must be
  * below 0.6 rho0 (the two-step-averaged exchange of one face pair is stable
@@ -225,17 +229,23 @@ int klb_bounds_checked(void);
  * cannot join a batch. */
 klb_status klb_set_fluctuations(klb_lattice *lat, double kT, uint64_t seed);
 
-/* Start from the local equilibrium of host fields in box layout:
+/* Start from the local equilibrium (Sec. 4: the second-order polynomial
+ * equilibrium of every species, in deviation form) of host fields in box layout:
  * drho[3][ncell] density deviations and u[3][3][ncell] velocities (either
  * may be NULL for zero).  The lagged interface velocities are set to u.
  * Resets the step counter to 0.  Synchronises the stream. */
 klb_status klb_init_equilibrium(klb_lattice *lat, const double *drho, const double *u);
 
-/* Advance nsteps >= 0 lattice steps (stream + collide + interface coupling of
- * all three species, one fused kernel per step).  Asynchronous. */
+/* Advance nsteps >= 0 lattice steps of Sec. 4 (pull streaming with the
+ * boundary rules of Sec. 4.2, BGK collision with the drive of Eq. 2 by Guo
+ * forcing, interface friction of Eq. 27 from lagged velocities, co-located
+ * electron-phonon friction and crystal sinks of Eqs. 12-16) for all three
+ * species, one fused kernel per step.  Asynchronous. */
 klb_status klb_step(klb_lattice *lat, int64_t nsteps);
 
-/* Compute the observables of the current step into *out (host).
+/* Compute the observables of the current step into *out (host): the slip
+ * length L_s = u_s / (du/dy)_w of Sec. 1 from a fit of the water profile,
+ * the flow rate, and the species means, masses and momenta (FP64 sums).
  * Synchronises the stream.  Returns KLB_EUNSTABLE (with *out filled) when a
  * non-finite value was seen. */
 klb_status klb_observables(klb_lattice *lat, klb_obs *out);
@@ -272,11 +282,12 @@ klb_status klb_observables(klb_lattice *lat, klb_obs *out);
 #define KLB_STATIC_MAX_BLOCKS 49152
 klb_status klb_observables_static(klb_lattice *lat, klb_obs *out);
 
-/* Density deviations drho[3][ncell] and velocities u[3][3][ncell] of the
- * current step, host, box layout (either may be NULL).  Synchronises. */
+/* Density deviations drho[3][ncell] and velocities u[3][3][ncell] (the
+ * moments of Sec. 4, with the half-force correction of the Guo velocity) of
+ * the current step, host, box layout (either may be NULL).  Synchronises. */
 klb_status klb_get_field(klb_lattice *lat, double *drho, double *u);
 
-/* Current state to host, box layout: post-collision deviations
+/* Checkpoints (no counterpart in the paper).  Current state to host, box layout: post-collision deviations
  * g[3][Q][ncell] and the velocities of the two previous steps
  * U1[3][3][ncell] = u(n-1), U2 = u(n-2).  The lagged velocities are kept
  * only at interface cells; other cells read 0.  Any pointer may be NULL.
@@ -289,9 +300,10 @@ klb_status klb_set_state(klb_lattice *lat, const double *g, const double *U1,
                          const double *U2, int64_t step);
 
 /*
- * Batches: many independent lattices stepped together, one kernel launch per
- * lattice step for all of them (design sweeps over channels of different
- * sizes and parameters).  All members share the lattice kind, the storage
+ * Batches (no counterpart in the paper; they serve design sweeps in the
+ * shape of the nanotube study of Sec. 5.1): many independent lattices
+ * stepped together, one kernel launch per lattice step for all of them
+ * (channels of different sizes and parameters).  All members share the lattice kind, the storage
  * type and the CUDA stream; they may stand at different time levels (a
  * request admitted while others run).  A member's step pattern (state buffer
  * parity, lagged-velocity ring slot and, for 16-bit storage, reference
@@ -440,11 +452,13 @@ klb_status klb_server_destroy(klb_server *srv);
  * for a failed creation when srv is NULL. */
 const char *klb_server_last_error(const klb_server *srv);
 
-/* Number of completed steps, lattice sizes and species-cell counts. */
+/* Number of completed steps, lattice sizes and species-cell counts
+ * (bookkeeping, no counterpart in the paper). */
 int64_t klb_get_step(const klb_lattice *lat);
 int64_t klb_species_cells(const klb_lattice *lat, int species);
 
-/* Release the handle (not the caller's buffer).  Synchronises. */
+/* Release the handle (not the caller's buffer).  Synchronises.  No
+ * counterpart in the paper, as for the error messages below. */
 klb_status klb_destroy(klb_lattice *lat);
 
 /* Message of the last failing call on `lat` ("" if none); a message for
