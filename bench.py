@@ -125,7 +125,7 @@ class ClockSampler:
             except ValueError:
                 continue
         if not rows:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k] == "Active"})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],

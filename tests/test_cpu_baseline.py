@@ -57,3 +57,22 @@ def test_profile_traffic_follows_the_kernel_sources(monkeypatch):
     assert t is None or 0.95 * algorithmic < t < 1.05 * algorithmic
     monkeypatch.setattr(bench, "_kernel_source_hash", lambda: "0" * 16)
     assert bench._ncu_traffic() is None
+
+
+def test_clock_summary_parsing():
+    """The clocks object of the benchmark line: median SM clock under load,
+    the maximum clock, and every throttle reason seen active."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    c = bench.ClockSampler(0)
+    c.out = ("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+             "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+             "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+             "garbage line\n")
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.out = ""
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}

@@ -19,14 +19,14 @@ def test_default_bench_line():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    r = subprocess.run([sys.executable, "bench.py", "--steps", "3", "--warmup", "3"], cwd=ROOT,
+    r = subprocess.run([sys.executable, "bench.py", "--steps", "6", "--warmup", "3"], cwd=ROOT,
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-3000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["metric"] == "MLUPS" and d["unit"] == "MLUPS" and d["higher_is_better"] is True
-    assert d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3 and d["scaling"] == "weak"
+    assert d["n_gpus"] == 1 and d["steps"] == 6 and d["warmup"] == 3 and d["scaling"] == "weak"
     assert d["value"] > 0 and d["ms_per_step"] > 0 and d["data"] == "synthetic" and d["dtype"] == "f32"
     assert d["config"]["workload"] == "d3q19_fp32_pipe_512x128x128_r48"
     rf = d["roofline"]
@@ -38,6 +38,6 @@ def test_default_bench_line():
     assert e["unit"] == "MLUPS" and e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] > 0 and cb["cores"] >= 1 and cb["sample"]
-    assert d["gpu_launches"] == 3 * (100 + 2)
+    assert d["gpu_launches"] == 6 * (100 + 2)
     clk = d["clocks"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(clk)
