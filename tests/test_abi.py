@@ -235,3 +235,38 @@ def test_design_grid_recipe():
         assert klb.klb_lattice_bytes(klb.desc_from_workload(w)) > 0
     assert sorted({w.radius for w in ws}) == [6, 8, 12]
     assert sorted({w.couplings[0] for w in ws}) == [-0.02, 0.0, 0.05]
+
+
+def test_perturbation_recipe():
+    """drho = rho0 eps xi, u = eps eta, xi and eta uniform on (-1, 1) from
+    default_rng(seed) in that order, box layout; no z velocity on D2Q9."""
+    w = inputs.SLAB_D2Q9_FP64
+    d, u = inputs.perturbation(w, 7, 1e-3)
+    rng = np.random.default_rng(7)
+    xi = rng.uniform(-1.0, 1.0, (3, w.nz, w.ny, w.nx))
+    eta = rng.uniform(-1.0, 1.0, (3, 3, w.nz, w.ny, w.nx))
+    assert d.shape == (3, w.nz, w.ny, w.nx) and u.shape == (3, 3, w.nz, w.ny, w.nx)
+    assert np.array_equal(d, w.rho0 * 1e-3 * xi)
+    assert np.array_equal(u[:, :2], 1e-3 * eta[:, :2]) and not u[:, 2].any()
+    d3, u3 = inputs.perturbation(inputs.PIPE_D3Q19_SUB, 7, 1e-3)
+    assert np.abs(u3[:, 2]).max() > 0 and np.abs(d3).max() <= 1e-3
+
+
+def test_channel_sweep_recipe():
+    """96 channels: slab or pipe (about half each), nx in [64, 512], box
+    sides in [16, 128] (a pipe's box widened to fit its shell), shell in
+    [2, 8], tau_w in [0.55, 1.2], drive in [1e-7, 1e-5], couplings in
+    [1e-4, 1e-1] with g_ec = 0, and every channel inside the interface
+    stability bound (at most two solid faces per fluid cell)."""
+    ws = inputs.channel_sweep(96, seed=0)
+    assert len(ws) == 96 and 30 <= sum(w.geom == "pipe" for w in ws) <= 66
+    for w in ws:
+        assert 64 <= w.nx <= 512 and 2 <= w.shell <= 8 and 16 <= w.nz <= 128
+        assert 0.55 <= w.tau[0] <= 1.2 and w.tau[1:] == (0.6, 1.0)
+        assert 1e-7 <= w.G[0] <= 1e-5 and w.G[1:] == (0.0, 0.0)
+        g_we, g_wp, g_ep, g_ec, g_pc = w.couplings
+        assert g_ec == 0.0 and all(1e-4 <= g <= 1e-1 for g in (g_we, g_wp, g_ep, g_pc))
+        info = klb.klb_lattice_info(klb.desc_from_workload(w))
+        assert info["max_faces"][0] <= 2
+        assert info["max_faces"][0] * (g_we + g_wp) < 0.6 * w.rho0
+    assert inputs.channel_sweep(96, seed=0) == ws and inputs.channel_sweep(96, seed=1) != ws
