@@ -685,6 +685,22 @@ def test_negative_friction_steady_slab():
 # Thermal fluctuations (Eq. 6, Eq. 17): the generator, exact conservation,
 # and equipartition of the fluctuating lattice fluid.
 
+def test_philox_known_answer_vectors():
+    """The oracle's Philox-4x32-10 reproduces the generator's published
+    known-answer vectors (Salmon et al., SC 2011; fixture
+    tests/golden/philox4x32_10_kat.txt): a swapped output word, a wrong
+    multiplier or Weyl constant, or a wrong round count changes every word."""
+    from oracle.oracle import philox4x32_10
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        got = [int(x) for x in philox4x32_10(v[0:4], v[4:6])]
+        assert got == v[6:10], (r, [f"{x:08x}" for x in got])
+
+
 def test_philox_generator_statistics():
     """Philox-4x32-10 words are uniform, uncorrelated between neighbouring
     counters and words, distinct over a sample of counters (the map is a
