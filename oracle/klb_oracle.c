@@ -67,6 +67,7 @@ typedef struct {
     double *u[3];    /* velocity of the current step, [a*ncell + cell] */
     double *F[3];    /* total force density of the current step        */
     long step;
+    int phonon_wave; /* 1: phonons follow the damped wave equation of Sec. 3.4 */
     double kT;       /* thermal energy of the water fluctuations (0: off) */
     uint32_t key[2]; /* generator key (seed)                              */
 } kor_t;
@@ -436,6 +437,44 @@ static double geq(const kor_t *o, int i, double drho, const double u[3])
     return o->w[i] * (drho + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
 }
 
+/*
+ * Phonons as linear waves (Sec. 3.4): their density obeys the damped wave
+ * equation  d_tt n_p - cs^2 d_xx n_p = -gamma_p d_t n_p,  with
+ * gamma_p = gamma_pC + gamma_pe (1 - u_e/u_p) the sum of the friction rates.
+ * A population set relaxing to an equilibrium that is linear in the
+ * momentum,
+ *   g^eq_i = w_i [drho + 3 c_i . (rho u)],
+ * has the moments drho, rho u and cs^2 drho I (no convective flux rho u u),
+ * so continuity d_t n + div j = 0 and momentum d_t j = -cs^2 grad n + F
+ * (plus the BGK viscous term) combine into that wave equation once the
+ * friction force F of the phonons is inserted.  The forcing term carries only
+ * its first moment, (1 - omega/2) w_i 3 c_i . F (the second-moment terms of
+ * the Guo source balance the u u part of the second-order equilibrium, which
+ * the linear one lacks).
+ */
+static int wave_species(const kor_t *o, int s) { return s == SP && o->phonon_wave; }
+
+static double geq_species(const kor_t *o, int s, int i, double drho, const double u[3])
+{
+    if (!wave_species(o, s)) return geq(o, i, drho, u);
+    double rho = o->rho0 + drho;
+    double cu = o->c[i][0] * u[0] + o->c[i][1] * u[1] + o->c[i][2] * u[2];
+    return o->w[i] * (drho + 3.0 * rho * cu);
+}
+
+static double guo_species(const kor_t *o, int s, int i, double om, const double u[3],
+                          const double F[3])
+{
+    const int *c = o->c[i];
+    double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+    double cF = c[0] * F[0] + c[1] * F[1] + c[2] * F[2];
+    double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    if (wave_species(o, s)) return (1.0 - 0.5 * om) * o->w[i] * 3.0 * cF;
+    return (1.0 - 0.5 * om) * o->w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+}
+
+void kor_set_phonon_wave(kor_t *o, int on) { o->phonon_wave = on != 0; }
+
 /* Start from the local equilibrium of the given fields (dense boxes, one
  * density deviation and three velocity components per species).  The lagged
  * velocities of "steps -1 and -2" are the initial velocity. */
@@ -456,7 +495,7 @@ void kor_init_equilibrium(kor_t *o, const double *drho /* [3][ncell] */,
                     double dr = drho ? drho[s * N + k] : 0.0;
                     double v[3] = {0, 0, 0};
                     for (int a = 0; a < 3 && u; a++) v[a] = u[(s * 3 + a) * N + k];
-                    for (int i = 0; i < o->Q; i++) o->gs[s][i * N + k] = geq(o, i, dr, v);
+                    for (int i = 0; i < o->Q; i++) o->gs[s][i * N + k] = geq_species(o, s, i, dr, v);
                     for (int a = 0; a < 3; a++) o->U[s][a * N + k] = v[a];
                     for (int a = 0; a < 3; a++) o->U2[s][a * N + k] = v[a];
                 }
@@ -585,7 +624,8 @@ static void stream_and_velocities(kor_t *o)
 }
 
 /* 6. BGK collision with Guo forcing:
- *    g*_i = g_i + omega (g^eq_i - g_i) + (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F */
+ *    g*_i = g_i + omega (g^eq_i - g_i) + (1 - omega/2) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F
+ *    (phonons of the wave variant: the linear equilibrium and source above) */
 static void collide(kor_t *o)
 {
     const long N = o->ncell;
@@ -602,17 +642,10 @@ static void collide(kor_t *o)
                         v[a] = o->u[s][a * N + k];
                         Fv[a] = o->F[s][a * N + k];
                     }
-                    double uF = v[0] * Fv[0] + v[1] * Fv[1] + v[2] * Fv[2];
-                    double uu = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                    double dr = o->drho[s][k], rho = o->rho0 + dr;
+                    double dr = o->drho[s][k];
                     for (int i = 0; i < o->Q; i++) {
-                        const int *c = o->c[i];
-                        double cu = c[0] * v[0] + c[1] * v[1] + c[2] * v[2];
-                        double cF = c[0] * Fv[0] + c[1] * Fv[1] + c[2] * Fv[2];
-                        /* same polynomial as geq() */
-                        double eq = o->w[i] * (dr + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
-                        double Fi = (1.0 - 0.5 * om) * o->w[i] *
-                                    (3.0 * (cF - uF) + 9.0 * cu * cF);
+                        double eq = geq_species(o, s, i, dr, v);
+                        double Fi = guo_species(o, s, i, om, v, Fv);
                         double gi = o->g[s][i * N + k];
                         o->gs[s][i * N + k] = gi + om * (eq - gi) + Fi;
                     }
@@ -725,6 +758,20 @@ double kor_geq(const kor_t *o, int i, double drho, double ux, double uy, double 
 {
     double u[3] = {ux, uy, uz};
     return geq(o, i, drho, u);
+}
+
+/* The same for one species (the phonons differ under the wave variant). */
+double kor_geq_species(const kor_t *o, int s, int i, double drho, double ux, double uy, double uz)
+{
+    double u[3] = {ux, uy, uz};
+    return geq_species(o, s, i, drho, u);
+}
+
+double kor_guo_species(const kor_t *o, int s, int i, double omega, double ux, double uy, double uz,
+                       double Fx, double Fy, double Fz)
+{
+    double u[3] = {ux, uy, uz}, F[3] = {Fx, Fy, Fz};
+    return guo_species(o, s, i, omega, u, F);
 }
 
 double kor_guo(const kor_t *o, int i, double omega, double ux, double uy, double uz,

@@ -18,7 +18,10 @@ momentum balance per step; closed-form special cases (free acceleration,
 Crank-Nicolson e-p relaxation, lagged water-electron pair); the magic-tau
 bounce-back parabola; bulk curvature; wall force balance; an independent
 dense steady-state solve of the slab; slip-Poiseuille closed forms; D3Q19
-slab = D2Q9 slab; eight-fold pipe symmetry.  Parity unpinned: the
+slab = D2Q9 slab; eight-fold pipe symmetry; the phonon damped-wave variant
+of Sec. 3.4 (moments of its linear equilibrium, the decay rate and frequency
+of a single Fourier mode of the damped wave equation, no advection by a
+uniform phonon flow).  Parity unpinned: the
 Bose-Einstein / Fermi-Dirac specific corrections to the equilibria, which the
 paper does not give and which are therefore not implemented.
 """
@@ -83,6 +86,11 @@ def _load():
     lib.kor_geq.argtypes = [P, I, D, D, D, D]
     lib.kor_guo.restype = D
     lib.kor_guo.argtypes = [P, I, D, D, D, D, D, D, D]
+    lib.kor_geq_species.restype = D
+    lib.kor_geq_species.argtypes = [P, I, I, D, D, D, D]
+    lib.kor_guo_species.restype = D
+    lib.kor_guo_species.argtypes = [P, I, I, D, D, D, D, D, D, D]
+    lib.kor_set_phonon_wave.argtypes = [P, I]
     _lib = lib
     return lib
 
@@ -166,7 +174,7 @@ class Oracle:
 
     def __init__(self, Q: int, nx: int, geo: Geometry, tau=(0.8, 0.6, 1.0), rho0=1.0,
                  G=(0.0, 0.0, 0.0), couplings=(0.0, 0.0, 0.0, 0.0, 0.0),
-                 iface_bounceback=False):
+                 iface_bounceback=False, phonon_wave=False):
         lib = _load()
         self.Q, self.nx, self.geo = Q, nx, geo
         self.ny, self.nz = geo.ny, geo.nz
@@ -182,6 +190,8 @@ class Oracle:
         self._h = ctypes.c_void_p(h)
         lib.kor_set_params(self._h, tau[0], tau[1], tau[2], rho0, G[0], G[1], G[2],
                            int(bool(iface_bounceback)))
+        lib.kor_set_phonon_wave(self._h, int(bool(phonon_wave)))
+        self.phonon_wave = bool(phonon_wave)
         self.set_couplings(*couplings)
 
     def __del__(self):
@@ -257,6 +267,14 @@ class Oracle:
 
     def guo(self, i, omega, u, F):
         return _lib.kor_guo(self._h, i, omega, u[0], u[1], u[2], F[0], F[1], F[2])
+
+    def geq_species(self, s, i, drho, u):
+        """Equilibrium of direction i for species s (the phonons' is linear
+        under the damped-wave variant of Sec. 3.4)."""
+        return _lib.kor_geq_species(self._h, s, i, drho, u[0], u[1], u[2])
+
+    def guo_species(self, s, i, omega, u, F):
+        return _lib.kor_guo_species(self._h, s, i, omega, u[0], u[1], u[2], F[0], F[1], F[2])
 
     def species_mask(self, s):
         t = T_FLUID if s == WATER else T_SOLID

@@ -205,10 +205,11 @@ def _post_momentum(o):
     return np.einsum("sik,i->s", gs.reshape(3, o.Q, -1), c[:, 0].astype(float))
 
 
+@pytest.mark.parametrize("wave", [False, True])
 @pytest.mark.parametrize("Q,nx,geo", list(_geometries()))
-def test_mass_conserved_per_step(Q, nx, geo):
+def test_mass_conserved_per_step(Q, nx, geo, wave):
     o = Oracle(Q, nx, geo, tau=(0.7, 0.6, 1.1), G=(1e-5, 2e-6, 0.0),
-               couplings=(0.05, 0.02, 0.1, 0.003, 0.01))
+               couplings=(0.05, 0.02, 0.1, 0.003, 0.01), phonon_wave=wave)
     _perturbed(o)
     gs0, _, _ = o.get_state()
     m0 = gs0.reshape(3, -1).sum(1)
@@ -218,15 +219,17 @@ def test_mass_conserved_per_step(Q, nx, geo):
         assert np.abs(gs.reshape(3, -1).sum(1) - m0).max() < 1e-15
 
 
+@pytest.mark.parametrize("wave", [False, True])
 @pytest.mark.parametrize("Q", [9, 19])
-def test_momentum_balance_without_outer_walls(Q):
+def test_momentum_balance_without_outer_walls(Q, wave):
     """No void anywhere (periodic in y): the only x-momentum sources are the
     drive on the fluid and the crystal sinks; interface and electron-phonon
-    friction cancel pairwise (Eq. 27), specular links carry none."""
+    friction cancel pairwise (Eq. 27), specular links carry none.  The same
+    holds with the phonons of the damped-wave variant (Sec. 3.4)."""
     rows = [T_SOLID] * 3 + [T_FLUID] * 6 + [T_SOLID] * 2
     G = 3e-5
     o, geo = _mask(Q, 4, rows, tau=(0.7, 0.6, 1.1), G=(G, 0.0, 0.0),
-                   couplings=(0.05, 0.02, 0.1, 0.004, 0.01))
+                   couplings=(0.05, 0.02, 0.1, 0.004, 0.01), phonon_wave=wave)
     _perturbed(o)
     n_fluid = (geo.cs_type == T_FLUID).sum() * o.nx
     P0 = _post_momentum(o).sum()
@@ -413,6 +416,127 @@ def test_phonon_friction_identity():
     ue, up, Fp = f["u"][1, 0], f["u"][2, 0], f["F"][2, 0]
     gp = 0.05 + 0.2 * (1 - ue / up)
     assert np.abs(Fp - (-gp * up)).max() < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Phonons as linear damped waves (Sec. 3.4): the variant whose phonon
+# equilibrium is linear in the momentum, g^eq_i = w_i [drho + 3 c_i . rho u].
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_phonon_wave_moments(Q):
+    """The linear equilibrium has the moments drho, rho u and cs^2 drho I
+    (no convective flux rho u u), its forcing term 0, (1 - omega/2) F and 0;
+    water and electrons keep the second-order equilibrium."""
+    geo = cross_section("slab", 12, 1, width=4, shell=4) if Q == 9 else \
+        cross_section("pipe", 8, 8, radius=2, shell=1)
+    o = Oracle(Q, 1, geo, phonon_wave=True)
+    ref = Oracle(Q, 1, geo)
+    c, w, _ = o.lattice()
+    cf = c.astype(float)
+    d = 2 if Q == 9 else 3
+    I = np.eye(3)
+    I[d:, d:] = 0
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        drho = rng.uniform(-0.05, 0.05)
+        rho = 1.0 + drho
+        u = rng.uniform(-0.05, 0.05, 3)
+        F = rng.uniform(-1e-3, 1e-3, 3)
+        if Q == 9:
+            u[2] = F[2] = 0.0
+        om = rng.uniform(0.6, 1.9)
+        eq = np.array([o.geq_species(2, i, drho, u) for i in range(Q)])
+        S = np.array([o.guo_species(2, i, om, u, F) for i in range(Q)])
+        assert abs(eq.sum() - drho) < 1e-15
+        assert np.abs(cf.T @ eq - rho * u).max() < 1e-15
+        assert np.abs(np.einsum("i,ia,ib->ab", eq, cf, cf) - drho * CS2 * I).max() < 1e-15
+        assert abs(S.sum()) < 1e-16
+        assert np.abs(cf.T @ S - (1 - om / 2) * F).max() < 1e-16
+        assert np.abs(np.einsum("i,ia,ib->ab", S, cf, cf)).max() < 1e-17
+        for s in (0, 1):
+            for i in range(Q):
+                assert o.geq_species(s, i, drho, u) == ref.geq(i, drho, u)
+                assert o.guo_species(s, i, om, u, F) == ref.guo(i, om, u, F)
+
+
+def _phonon_chain(Q, nx, gamma_pc, tau_p=1.0, wave=True):
+    """A periodic chain of solid cells (one cross-section cell, periodic in
+    y and z): electrons and phonons only, no interface."""
+    geo = cross_section("mask", 1, 1, mask=np.array([[T_SOLID]], np.uint8), periodic_y=True,
+                        periodic_z=True)
+    return Oracle(Q, nx, geo, tau=(0.8, 0.6, tau_p), couplings=(0, 0, 0, 0, gamma_pc),
+                  phonon_wave=wave)
+
+
+def _damped_mode_fit(a):
+    """Decay rate and angular frequency of a sampled damped oscillation
+    a(n) = e^{-G n} (A cos w n + B sin w n), from the recurrence
+    a(n+1) = 2 e^{-G} cos(w) a(n) - e^{-2G} a(n-1) that it satisfies exactly
+    (Prony's method, least squares over all samples)."""
+    M = np.stack([a[1:-1], a[:-2]], 1)
+    p, *_ = np.linalg.lstsq(M, a[2:], rcond=None)
+    r = math.sqrt(-p[1])
+    return -math.log(r), math.acos(p[0] / (2 * r))
+
+
+@pytest.mark.parametrize("Q,gamma_pc,tau_p", [(19, 0.005, 1.0), (19, 0.01, 0.8), (9, 0.005, 1.0)])
+def test_phonon_damped_wave_mode(Q, gamma_pc, tau_p):
+    """A density mode n_p = eps cos(k x) of the phonon chain follows the damped
+    wave equation of Sec. 3.4, d_tt n - cs^2 d_xx n = -gamma_p d_t n (here
+    gamma_p = gamma_pC, no electron coupling), plus the BGK viscous damping of
+    a longitudinal mode: s^2 + (gamma + 2 nu k^2) s + cs^2 k^2 = 0, i.e. decay
+    rate (gamma + 2 nu k^2)/2 and frequency sqrt(cs^2 k^2 - decay^2), with
+    nu = cs^2 (tau_p - 1/2) and, for the trapezoidal sink, gamma =
+    2 atanh(gamma_pC / 2) (the per-step factor (1 - g/2)/(1 + g/2)).  The
+    lattice corrects both at O(k^2) = 6e-4 relative."""
+    nx = 256
+    o = _phonon_chain(Q, nx, gamma_pc, tau_p)
+    k = 2 * math.pi / nx
+    x = np.arange(nx)
+    drho = np.zeros((3, 1, 1, nx))
+    drho[2, 0, 0] = 1e-6 * np.cos(k * x)
+    o.init_equilibrium(drho, np.zeros((3, 3, 1, 1, nx)))
+    amp = []
+    for n in range(2000):
+        o.step(1)
+        amp.append(o.observe()["drho"][2, 0, 0] @ np.cos(k * x) * 2 / nx)
+    decay, freq = _damped_mode_fit(np.array(amp[50:]))
+    nu = CS2 * (tau_p - 0.5)
+    decay_th = (2 * math.atanh(gamma_pc / 2) + 2 * nu * k * k) / 2
+    freq_th = math.sqrt(CS2 * k * k - decay_th ** 2)
+    assert decay == pytest.approx(decay_th, rel=1e-4)
+    assert freq == pytest.approx(freq_th, rel=3e-4)
+    # the sink is what damps the wave: half the rate without it
+    assert decay_th > 1.5 * nu * k * k
+
+
+@pytest.mark.parametrize("wave", [True, False])
+def test_phonon_wave_is_linear(wave):
+    """With no force the wave variant is a linear scheme: a density mode on
+    top of a uniform phonon flow evolves as the two evolve apart (a wave
+    equation has no advection term).  The second-order equilibrium advects
+    the mode (Doppler shift c_s +- u), so superposition fails by O(1)."""
+    nx = 64
+    k = 2 * math.pi / nx
+    x = np.arange(nx)
+    oa, ob, oc = (_phonon_chain(19, nx, 0.0, wave=wave) for _ in range(3))
+    drho = np.zeros((3, 1, 1, nx))
+    drho[2, 0, 0] = 1e-6 * np.cos(k * x)
+    u = np.zeros((3, 3, 1, 1, nx))
+    oa.init_equilibrium(drho, u)
+    u[2, 0] = 0.05
+    ob.init_equilibrium(np.zeros_like(drho), u)
+    ga, Ua, U2a = oa.get_state()
+    gb, Ub, U2b = ob.get_state()
+    oc.set_state(ga + gb, Ua + Ub, U2a + U2b, 0)
+    for o in (oa, ob, oc):
+        o.step(400)
+    ra, rb, rc = (o.observe()["drho"][2, 0, 0] for o in (oa, ob, oc))
+    err = np.abs(rc - rb - ra).max() / np.abs(ra).max()
+    if wave:
+        assert err < 1e-8
+    else:
+        assert err > 0.1
 
 
 # ---------------------------------------------------------------------------
