@@ -216,6 +216,89 @@ STORAGE_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp64": 8}
 NOISE_KT = 1e-5  # thermal energy of the nanotube_noise workload (lattice units)
 
 
+def _step_launch_ms(lat, stream, blocks, warmup=2):
+    """Mean time per step-kernel launch: CUDA events on the lattice's stream
+    around blocks of LATTICE_STEPS_PER_STEP steps (an observation pass after
+    each block, outside the events), after warm-up blocks."""
+    import torch
+
+    for _ in range(warmup):
+        lat.step(LATTICE_STEPS_PER_STEP)
+        lat.observables()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(blocks)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(stream)
+        lat.step(LATTICE_STEPS_PER_STEP)
+        b.record(stream)
+        lat.observables()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / (blocks * LATTICE_STEPS_PER_STEP)
+
+
+def _precision_block(dev, blocks=5):
+    """FP32 against 16-bit storage on the 768 x 192 x 192 nanotube (radius 72,
+    shell 9): per storage the step kernel's launch time, its site rate and
+    its fraction of the measured HBM bandwidth, and the 16-bit / FP32
+    ratios of the cell rate."""
+    import torch
+
+    from paper_2403_15768_gb300 import inputs, klb
+
+    peak, _ = _peaks()
+    out = {"workload": inputs.PIPE_D3Q19_LARGE.name, "timing": f"CUDA events around {blocks} blocks "
+           f"of {LATTICE_STEPS_PER_STEP} steps after 2 warm-up blocks"}
+    for storage in ("fp32", "fp16", "bf16"):
+        w = inputs.PIPE_D3Q19_LARGE.with_(storage=storage)
+        stream = torch.cuda.Stream(dev)
+        with torch.cuda.stream(stream):
+            lat = klb.lattice_from_workload(w, device=dev, stream=stream)
+            ms = _step_launch_ms(lat, stream, blocks)
+            sites = lat.active_sites()
+            cells = sum(lat.species_cells(s) for s in range(3))
+            lat.close()
+        nbytes = cells * 2 * 19 * STORAGE_BYTES[storage]
+        out[storage] = {"launch_ms": ms, "mlups": sites / (ms * 1e-3) / 1e6,
+                        "bytes_per_launch": nbytes,
+                        "roofline_frac": nbytes / (ms * 1e-3) / 1e9 / peak}
+        del lat
+        torch.cuda.empty_cache()
+    for storage in ("fp16", "bf16"):
+        out[f"{storage}_over_fp32"] = out[storage]["mlups"] / out["fp32"]["mlups"]
+    return out
+
+
+def _serving_block(dev, n=12):
+    """A short seeded trace of the request loop per storage (n requests of
+    the Poisson stream, 50 per second, seed 0, cells log-uniform in
+    [32^3, 512 x 128 x 128], run to the residual tolerance or 2 x 10^4
+    steps): p50 / p99 time to solution and aggregate MLUPS."""
+    import torch
+
+    from paper_2403_15768_gb300 import inputs, klb, serving
+
+    out = {"requests": n, "rate_per_s": 50.0, "max_steps": 20000, "check_every": 100}
+    for storage in ("fp32", "fp16"):
+        tol = 1e-9 if storage == "fp32" else 1e-7
+        stream = torch.cuda.Stream(dev)
+        with torch.cuda.stream(stream):
+            srv = klb.Server(40 * 10 ** 9, storage=storage, check_every=100, max_resident=128,
+                             device=dev, stream=stream)
+            serving.replay(srv, inputs.request_stream(2, rate=50.0, seed=1000, storage=storage,
+                                                      max_cells=64 ** 3), tol=tol, max_steps=1000)
+            run = serving.replay(srv, inputs.request_stream(n, rate=50.0, seed=0, storage=storage),
+                                 tol=tol, max_steps=20000)
+            srv.close()
+            del srv
+        summ = serving.summarise(run)
+        out[storage] = {"mlups": summ["site_updates"] / summ["makespan_s"] / 1e6, "tol": tol,
+                        **{k: summ[k] for k in ("p50_s", "p99_s", "makespan_s", "status")}}
+        torch.cuda.empty_cache()
+    out["fp16_over_fp32"] = out["fp16"]["mlups"] / out["fp32"]["mlups"]
+    return out
+
+
 def run(args):
     if args.workload.startswith("sweep_"):
         return run_sweep(args)
@@ -323,6 +406,12 @@ def run(args):
         "observables": {"flow_rate": obs["flow_rate"], "slip_length": obs["slip_length"],
                         "step": obs["step"], "e2e_step": obs_e2e["step"]},
     }
+    if args.workload == "nanotube" and not args.no_extras:
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        line["precision"] = _precision_block(dev)
+        line["serving"] = _serving_block(dev)
     if world == 1:
         line["cpu_baseline"] = _cpu_baseline(w)
     print(json.dumps(line), flush=True)
@@ -553,6 +642,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="nanotube", choices=WORKLOADS)
     ap.add_argument("--rate", type=float, default=50.0, help="serving: requests per second")
+    ap.add_argument("--no-extras", dest="no_extras", action="store_true",
+                    help="default workload: leave out the precision and serving blocks")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="sweeps: every channel length times this factor (1 = the 96-channel sweep)")
     args = ap.parse_args()

@@ -45,7 +45,9 @@ typedef enum {
     KLB_ECUDA = 3,     /* a CUDA call failed (message in klb_last_error)      */
     KLB_EUNSTABLE = 4, /* a non-finite value was seen                         */
     KLB_ETIMEOUT = 5,  /* reserved for step/time limits of callers            */
-    KLB_ESTATE = 6     /* call not valid in the handle's current state        */
+    KLB_ESTATE = 6,    /* call not valid in the handle's current state        */
+    KLB_ERANGE = 7     /* a 16-bit population difference left its range and
+                          was stored saturated (see klb_obs.clipped)          */
 } klb_status;
 
 enum { KLB_D2Q9 = 9, KLB_D3Q19 = 19 };
@@ -53,6 +55,7 @@ enum { KLB_GEOM_SLAB = 0, KLB_GEOM_PIPE = 1, KLB_GEOM_MASK = 2 };
 enum { KLB_FP64 = 0, KLB_FP32 = 1, KLB_FP16_DEV = 2, KLB_BF16_DEV = 3 };
 enum { KLB_IFACE_SPECULAR = 0, KLB_IFACE_BOUNCEBACK = 1 };
 enum { KLB_WATER = 0, KLB_ELECTRON = 1, KLB_PHONON = 2 };
+enum { KLB_PHONON_FLUID = 0, KLB_PHONON_WAVE = 1 };
 
 /*
  * Problem description (Sec. 2 set-up: water driven by a pressure gradient
@@ -79,6 +82,17 @@ enum { KLB_WATER = 0, KLB_ELECTRON = 1, KLB_PHONON = 2 };
  *   iface_bc  KLB_IFACE_SPECULAR (free slip at the liquid/solid interface
  *           for all species, Sec. 4.2) or KLB_IFACE_BOUNCEBACK (the Sec. 4.2
  *           alternative); outer solid faces always bounce back.
+ *   phonon_eq KLB_PHONON_FLUID (0, the default: the phonons relax to the
+ *           same second-order equilibrium as the other species) or
+ *           KLB_PHONON_WAVE: phonons as the linear waves of Sec. 3.4, whose
+ *           density obeys the damped wave equation
+ *             d_tt n_p - cs^2 d_xx n_p = -gamma_p d_t n_p
+ *           (gamma_p = gamma_pC + gamma_pe (1 - u_e/u_p), the friction rates
+ *           set by klb_set_couplings).  The phonon equilibrium is then linear
+ *           in the momentum, g^eq_i = w_i [drho + 3 c_i . rho u] (moments
+ *           drho, rho u and cs^2 drho I: no convective flux), and its forcing
+ *           term keeps only (1 - omega/2) w_i 3 c_i . F.  Any other value is
+ *           KLB_EINVAL.
  */
 typedef struct {
     int32_t kind;
@@ -94,6 +108,7 @@ typedef struct {
     double G[3];
     int32_t storage;
     int32_t iface_bc;
+    int32_t phonon_eq;
 } klb_desc;
 
 /*
@@ -127,6 +142,14 @@ typedef struct {
  *                  until two steps have run since creation, init or
  *                  klb_set_state.
  *   nonfinite      number of non-finite density/velocity values.
+ *   clipped        16-bit storage: number of species-cells holding a
+ *                  population at the largest finite 16-bit magnitude.  The
+ *                  encode saturates instead of overflowing to infinity: a
+ *                  stored difference (g - ref) * scale beyond +-65504 (FP16,
+ *                  scale 2^20: |g - ref| >= 65504 * 2^-20 = 0.0625, ref the
+ *                  row's x-average of that population) or +-3.39e38 (BF16,
+ *                  scale 1) is written as that bound.  Always 0 for FP32 and
+ *                  FP64 storage.
  * All sums are accumulated in FP64 on the device.
  */
 typedef struct {
@@ -140,6 +163,7 @@ typedef struct {
     double mass[3];
     double residual;
     int64_t nonfinite;
+    int64_t clipped;
 } klb_obs;
 
 /* Device bytes klb_create_lattice needs for this description (0 if the
@@ -247,7 +271,9 @@ klb_status klb_step(klb_lattice *lat, int64_t nsteps);
  * length L_s = u_s / (du/dy)_w of Sec. 1 from a fit of the water profile,
  * the flow rate, and the species means, masses and momenta (FP64 sums).
  * Synchronises the stream.  Returns KLB_EUNSTABLE (with *out filled) when a
- * non-finite value was seen. */
+ * non-finite value was seen, else KLB_ERANGE (with *out filled) when a 16-bit
+ * population was stored saturated (out->clipped > 0): the state is then no
+ * longer the scheme's. */
 klb_status klb_observables(klb_lattice *lat, klb_obs *out);
 
 /*
@@ -262,8 +288,8 @@ klb_status klb_observables(klb_lattice *lat, klb_obs *out);
  * Same inputs and output as klb_observables() (the lattice state is read, the
  * observables are written to *out on the host).  The per-block FP64 partial
  * sums and the final sums live in a static device array of this library
- * instead of the lattice buffer: KLB_STATIC_MAX_BLOCKS blocks of 18 doubles
- * plus 32 doubles (about 7.1 MB), held on every GPU that loads the library
+ * instead of the lattice buffer: KLB_STATIC_MAX_BLOCKS blocks of 19 doubles
+ * plus 32 doubles (about 7.5 MB), held on every GPU that loads the library
  * until the process exits.  Nothing is allocated: no cudaMalloc, cudaFree or
  * allocating library routine is called.
  *

@@ -136,6 +136,7 @@ void fill_args_at(const klb_lattice *L, const HostState &st, int sbx, StepArgs<T
     a.g_ep = (T)L->cp.g_ep;
     a.g_ec = (T)L->cp.g_ec;
     a.g_pc = (T)L->cp.g_pc;
+    a.q_p = (T)(d.phonon_eq == KLB_PHONON_WAVE ? 0.0 : 1.0);
     a.partials = (double *)dev(L, p.partials);
     a.residual_valid = st.since_reset >= 2;
     a.field = (T *)dev(L, p.field);
@@ -296,8 +297,9 @@ klb_status init_from_fields(klb_lattice *L, const double *drho, const double *u)
     return sync(L);
 }
 
-// Observables from the final sums, for klb_observables_static (the same
-// definitions as klb_observables).
+// Observables from the final sums (least squares u = A + B d^2 from its
+// normal equations, means, residual, non-finite count); the one definition
+// behind klb_observables and klb_observables_static.
 klb_status finish_observables(klb_lattice *L, const double *S, klb_obs *out)
 {
     const Geometry &g = L->geo;
@@ -331,7 +333,13 @@ klb_status finish_observables(klb_lattice *L, const double *S, klb_obs *out)
     }
     out->residual = L->st.since_reset >= 2 ? S[kSumResidual] : nan;
     out->nonfinite = (int64_t)S[kSumNonfinite];
+    out->clipped = (int64_t)S[kSumClipped];
     if (out->nonfinite > 0) return fail(L, KLB_EUNSTABLE, "non-finite density or velocity");
+    if (out->clipped > 0)
+        return fail(L, KLB_ERANGE,
+                    std::to_string(out->clipped) +
+                        " species-cells hold a population saturated at the 16-bit range (a difference "
+                        "from the row's x-average beyond the representable range)");
     return KLB_OK;
 }
 
@@ -540,41 +548,7 @@ klb_status klb_observables(klb_lattice *L, klb_obs *out)
                                 L->stream));
     klb_status st = sync(L);
     if (st != KLB_OK) return st;
-
-    const Geometry &g = L->geo;
-    const double nan = std::numeric_limits<double>::quiet_NaN();
-    std::memset(out, 0, sizeof *out);
-    out->step = L->st.step;
-    out->flow_rate = S[kSumUxFluid] / g.nx;
-    out->d_wall = g.has_fit ? g.d_wall : nan;
-    // Least squares u = A + B d^2 from its normal equations.
-    const double n = S[kSumFitN], s2 = S[kSumFitD2], s4 = S[kSumFitD4];
-    const double su = S[kSumFitU], su2 = S[kSumFitUD2];
-    const double det = n * s4 - s2 * s2;
-    if (g.has_fit && n >= 2 && det != 0.0) {
-        out->fit_B = (n * su2 - s2 * su) / det;
-        out->fit_A = (su - out->fit_B * s2) / n;
-        out->u_slip = out->fit_A + out->fit_B * g.d_wall * g.d_wall;
-        out->dudn_wall = std::fabs(2.0 * out->fit_B * g.d_wall);
-        out->slip_length = out->dudn_wall != 0.0 ? out->u_slip / out->dudn_wall
-                                                 : std::numeric_limits<double>::infinity();
-    } else {
-        out->fit_A = out->fit_B = out->u_slip = out->dudn_wall = out->slip_length = nan;
-    }
-    out->u_wallrow_mean = S[kSumWallN] > 0 ? S[kSumWallU] / S[kSumWallN] : nan;
-    const double ncells[3] = {(double)g.rows[kFluid].size() * g.nx,
-                              (double)g.rows[kSolid].size() * g.nx,
-                              (double)g.rows[kSolid].size() * g.nx};
-    const double usum[3] = {S[kSumUxFluid], S[kSumUxE], S[kSumUxP]};
-    for (int s = 0; s < 3; ++s) {
-        out->mean_u[s] = usum[s] / ncells[s];
-        out->momentum[s] = S[kSumMomW + s];
-        out->mass[s] = S[kSumMassW + s];
-    }
-    out->residual = L->st.since_reset >= 2 ? S[kSumResidual] : nan;
-    out->nonfinite = (int64_t)S[kSumNonfinite];
-    if (out->nonfinite > 0) return fail(L, KLB_EUNSTABLE, "non-finite density or velocity");
-    return KLB_OK;
+    return finish_observables(L, S, out);
 }
 
 klb_status klb_observables_static(klb_lattice *L, klb_obs *out)
@@ -735,6 +709,7 @@ klb_status klb_set_state(klb_lattice *L, const double *gin, const double *U1, co
     const int Q = g.Q;
     const bool red = reduced(L);
     const double scale = L->desc.storage == KLB_FP16_DEV ? kFp16Scale : 1.0;
+    auto sat = [](float v, float m) { return v > m ? m : (v < -m ? -m : v); };  // NaN passes
     auto put = [&](std::vector<char> &raw, size_t k, double v) {
         switch (L->desc.storage) {
         case KLB_FP64:
@@ -743,11 +718,11 @@ klb_status klb_set_state(klb_lattice *L, const double *gin, const double *U1, co
         case KLB_FP32:
             ((float *)raw.data())[k] = (float)v;
             break;
-        case KLB_FP16_DEV:
-            ((__half *)raw.data())[k] = __float2half_rn((float)v);
+        case KLB_FP16_DEV:  // saturating, as the device encode
+            ((__half *)raw.data())[k] = __float2half_rn(sat((float)v, 65504.0f));
             break;
         default:
-            ((__nv_bfloat16 *)raw.data())[k] = __float2bfloat16_rn((float)v);
+            ((__nv_bfloat16 *)raw.data())[k] = __float2bfloat16_rn(sat((float)v, 3.38953139e38f));
             break;
         }
     };

@@ -96,6 +96,8 @@ bool build_geometry(const klb_desc &d, Geometry &g, std::string &err)
         return err = "storage must be KLB_FP64, KLB_FP32, KLB_FP16_DEV or KLB_BF16_DEV", false;
     if (d.iface_bc != KLB_IFACE_SPECULAR && d.iface_bc != KLB_IFACE_BOUNCEBACK)
         return err = "iface_bc must be SPECULAR or BOUNCEBACK", false;
+    if (d.phonon_eq != KLB_PHONON_FLUID && d.phonon_eq != KLB_PHONON_WAVE)
+        return err = "phonon_eq must be KLB_PHONON_FLUID or KLB_PHONON_WAVE", false;
     double taus[3] = {d.tau_w, d.tau_e, d.tau_p};
     if (!finite_all(taus, 3) || !finite_all(&d.rho0, 1) || !finite_all(d.G, 3))
         return err = "non-finite tau, rho0 or G", false;

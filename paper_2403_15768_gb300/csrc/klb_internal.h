@@ -62,6 +62,7 @@ enum SumIndex {
     kSumMassP,
     kSumNonfinite,     // count of non-finite rho/u values
     kSumResidual,      // max |u_x(n) - u_x(n-1)| (a max, not a sum)
+    kSumClipped,       // 16-bit storage: species-cells with a saturated population
     kNumSums
 };
 
@@ -147,6 +148,7 @@ struct alignas(16) StepArgs {
     int n_rows[2], n_slots[2];
     T rho0, om[3], G[3];
     T g_we, g_wp, g_ep, g_ec, g_pc;
+    T q_p;                 // phonons: 1 second-order equilibrium, 0 linear (damped waves, Sec. 3.4)
     double *partials;      // observe mode: [block][kNumSums]
     int residual_valid;
     T *field;              // field / init mode: per species [4][n_rows][nxp]

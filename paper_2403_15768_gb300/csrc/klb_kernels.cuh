@@ -100,23 +100,80 @@ template <> struct Storage<double> {
     __device__ static double load(const double *p) { return __ldg(p); }
     __device__ static void store(double *p, double v) { *p = v; }
 };
+// 16-bit encodes round to nearest and saturate: a value beyond the largest
+// finite magnitude is stored as that magnitude (not as infinity), which the
+// observation pass counts (clipped_cell); NaN stays NaN.
+__device__ __forceinline__ unsigned short f32_to_f16_sat(float v)
+{
+    unsigned short r;
+    asm("cvt.rn.satfinite.f16.f32 %0, %1;" : "=h"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned short f32_to_bf16_sat(float v)
+{
+    unsigned short r;
+    asm("cvt.rn.satfinite.bf16.f32 %0, %1;" : "=h"(r) : "f"(v));
+    return r;
+}
+// Pairs: the low half holds v.x, the high half v.y.
+__device__ __forceinline__ unsigned f32x2_to_f16x2_sat(float2 v)
+{
+    unsigned r;
+    asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(v.y), "f"(v.x));
+    return r;
+}
+__device__ __forceinline__ unsigned f32x2_to_bf16x2_sat(float2 v)
+{
+    unsigned r;
+    asm("cvt.rn.satfinite.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(v.y), "f"(v.x));
+    return r;
+}
+
 template <> struct Storage<__half> {
     static constexpr bool kRef = true;
+    static constexpr unsigned short kMaxBits = 0x7bffu;  // 65504
     __device__ static float load(const __half *p)
     {
         return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p))));
     }
-    __device__ static void store(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static void store(__half *p, float v)
+    {
+        *reinterpret_cast<unsigned short *>(p) = f32_to_f16_sat(v);
+    }
 };
 template <> struct Storage<__nv_bfloat16> {
     static constexpr bool kRef = true;
+    static constexpr unsigned short kMaxBits = 0x7f7fu;  // 3.3895e38
     __device__ static float load(const __nv_bfloat16 *p)
     {
         return __bfloat162float(
             __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p))));
     }
-    __device__ static void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static void store(__nv_bfloat16 *p, float v)
+    {
+        *reinterpret_cast<unsigned short *>(p) = f32_to_bf16_sat(v);
+    }
 };
+
+// Whether any of the Q pulled 16-bit populations of a cell sits at the
+// largest finite magnitude (a saturated encode); false for wider storage.
+template <int Q, typename S>
+__device__ __forceinline__ bool clipped_cell(const S *__restrict__ in, const RowInfo &R, int x, int xm1, int xp1)
+{
+    if constexpr (!Storage<S>::kRef) {
+        return false;
+    } else {
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int xs = ((R.xm >> i) & 1u) ? xm1 : (((R.xp >> i) & 1u) ? xp1 : x);
+            const unsigned short b =
+                __ldg(reinterpret_cast<const unsigned short *>(in + (long long)R.src[i] * kRowAlign + xs));
+            any |= (b & 0x7fffu) == Storage<S>::kMaxBits;
+        }
+        return any;
+    }
+}
 
 // ---------------------------------------------------------------------------
 
@@ -197,23 +254,35 @@ __device__ __forceinline__ const float *ref_row(const float *table, int row)
 // BGK with Guo forcing, deviation form:
 // g*_i = g_i + om (geq_i - g_i) + (1 - om/2) w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F,
 // geq_i = w_i [drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)].
+// q scales every term of second order in u (and the matching u.F, (c.u)(c.F)
+// terms of the source): q = 1 is the scheme above (multiplying by 1 and 9 * 1
+// is exact, so its results do not change); q = 0 gives the linear equilibrium
+// w_i [drho + 3 rho c.u] and source (1 - om/2) w_i 3 c.F of phonons as the
+// damped linear waves of Sec. 3.4.
 // The exact scheme conserves mass and gives post-collision momentum j + F.
 // In FP32 the lattice weights (1/18, 1/36, ...) are not representable, and
 // the rounded weights bias both moments by the same relative amount in every
 // cell and every step, a drift that accumulates over the slow relaxation of
 // the channel flow.  FP32 therefore restores the two moments after the
 // collision: the mass residual goes to the rest population, the momentum
-// residual of each axis to its pair of axis populations.  The remaining
-// rounding is unbiased.  g is left holding g*.
+// residual of each axis to its pair of axis populations.  The momentum
+// residual is formed as (j - p) + F, not (j + F) - p: j and p differ by about
+// F, so j - p is exact and F is added to a small number.  Rounding j + F
+// instead would put a systematic error on the state: j is a multiple of its
+// own ulp and F changes little from step to step, so RN(j + F) - (j + F)
+// repeats with the same sign in every cell of a plug flow and every step
+// (for u in [2^-8, 2^-7) and F = 1e-6 it is -0.48 ulp(j), -2.2e-4 F; the
+// velocity drifts by that fraction of the drive).  The remaining rounding is
+// unbiased.  g is left holding g*.
 template <int Q, typename T>
-__device__ __forceinline__ void collide(T g[Q], const Cell<T> &c, const T j[3], T rho0, T om)
+__device__ __forceinline__ void collide(T g[Q], const Cell<T> &c, const T j[3], T rho0, T om, T q = T(1))
 {
     const T rho = rho0 + c.drho;
     const T uu = c.u[0] * c.u[0] + c.u[1] * c.u[1] + c.u[2] * c.u[2];
     const T uF = c.u[0] * c.F[0] + c.u[1] * c.F[1] + c.u[2] * c.F[2];
-    const T e0 = c.drho - T(1.5) * rho * uu;
-    const T r3 = T(3) * rho, r45 = T(4.5) * rho;
-    const T m3uF = T(-3) * uF;
+    const T e0 = c.drho - (T(1.5) * q) * rho * uu;
+    const T r3 = T(3) * rho, r45 = (T(4.5) * q) * rho;
+    const T m3uF = (T(-3) * q) * uF;
     const T om1 = T(1) - om;
     const T fo = T(1) - T(0.5) * om;
 #pragma unroll
@@ -226,7 +295,7 @@ __device__ __forceinline__ void collide(T g[Q], const Cell<T> &c, const T j[3], 
         const T cu = cdot<Q, T>(i, c.u);
         const T cF = cdot<Q, T>(i, c.F);
         const T teq = e0 + cu * (r3 + r45 * cu);
-        const T tF = m3uF + cF * (T(3) + T(9) * cu);
+        const T tF = m3uF + cF * (T(3) + (T(9) * q) * cu);
         g[i] = om1 * g[i] + (om * w) * teq + (fo * w) * tF;
     }
     if (sizeof(T) == 4) {
@@ -236,14 +305,14 @@ __device__ __forceinline__ void collide(T g[Q], const Cell<T> &c, const T j[3], 
         const T p[3] = {cmoment<Q, T>(0, g), cmoment<Q, T>(1, g),
                         Q == 19 ? cmoment<Q, T>(2, g) : T(0)};
         g[0] += c.drho - m;
-        const T hx = T(0.5) * ((j[0] + c.F[0]) - p[0]);
-        const T hy = T(0.5) * ((j[1] + c.F[1]) - p[1]);
+        const T hx = T(0.5) * ((j[0] - p[0]) + c.F[0]);
+        const T hy = T(0.5) * ((j[1] - p[1]) + c.F[1]);
         g[dir_index<Q>(1, 0, 0)] += hx;
         g[dir_index<Q>(-1, 0, 0)] -= hx;
         g[dir_index<Q>(0, 1, 0)] += hy;
         g[dir_index<Q>(0, -1, 0)] -= hy;
         if (Q == 19) {
-            const T hz = T(0.5) * ((j[2] + c.F[2]) - p[2]);
+            const T hz = T(0.5) * ((j[2] - p[2]) + c.F[2]);
             g[dir_index<Q>(0, 0, 1)] += hz;
             g[dir_index<Q>(0, 0, -1)] -= hz;
         }
@@ -467,6 +536,8 @@ __device__ inline void observe_reduce_store(const double (&s)[kNumSums], bool wa
     const int cnt = __syncthreads_count(live);
     const int nonfinite =
         __syncthreads_count(s[kSumNonfinite] >= 1.0) + __syncthreads_count(s[kSumNonfinite] >= 2.0);
+    const int clipped =
+        __syncthreads_count(s[kSumClipped] >= 1.0) + __syncthreads_count(s[kSumClipped] >= 2.0);
 #pragma unroll
     for (int k = 0; k < kNumSums; ++k) {
         if (!((sel >> k) & 1u)) continue;
@@ -498,6 +569,8 @@ __device__ inline void observe_reduce_store(const double (&s)[kNumSums], bool wa
             v = wall ? total(kSumUxFluid) : 0.0;
         else if (k == kSumNonfinite)
             v = (double)nonfinite;
+        else if (k == kSumClipped)
+            v = (double)clipped;
         out[k] = v;
     }
 }
@@ -580,6 +653,7 @@ __global__ void __launch_bounds__(kBlockX, (sizeof(T) == 4 ? 8 : 1)) k_lattice(c
                 s[kSumMomW] = rho * ux;
                 s[kSumMassW] = (double)c.drho;
                 s[kSumNonfinite] = finite3(c) ? 0.0 : 1.0;
+                s[kSumClipped] = clipped_cell<Q, S>(static_cast<const S *>(p.in[0]), R, x, xm1, xp1) ? 1.0 : 0.0;
                 if (R.flags & kFitRow) {
                     const double d2 = (double)R.d2;
                     s[kSumFitN] = 1.0;
@@ -630,6 +704,8 @@ __global__ void __launch_bounds__(kBlockX, (sizeof(T) == 4 ? 8 : 1)) k_lattice(c
                 s[kSumMassE] = (double)ce.drho;
                 s[kSumMassP] = (double)cp.drho;
                 s[kSumNonfinite] = (finite3(ce) ? 0.0 : 1.0) + (finite3(cp) ? 0.0 : 1.0);
+                s[kSumClipped] = (clipped_cell<Q, S>(static_cast<const S *>(p.in[1]), R, x, xm1, xp1) ? 1.0 : 0.0) +
+                                 (clipped_cell<Q, S>(static_cast<const S *>(p.in[2]), R, x, xm1, xp1) ? 1.0 : 0.0);
                 if (p.residual_valid) {
                     Cell<T> pe, pp;
                     pull<Q, T, S>(static_cast<const S *>(p.in_prev[1]), R, x, xm1, xp1,
@@ -697,7 +773,7 @@ __global__ void __launch_bounds__(kBlockX) k_init(const StepArgs<T> p)
 #pragma unroll
         for (int i = 0; i < Q; ++i) g[i] = T(0);
         for (int a = 0; a < 3; ++a) jeq[a] = (p.rho0 + c.drho) * c.u[a];
-        collide<Q, T>(g, c, jeq, p.rho0, T(1));
+        collide<Q, T>(g, c, jeq, p.rho0, T(1), s == 2 ? p.q_p : T(1));
         if constexpr (ACC) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) sums[k * Q + i] = float(g[i]);
@@ -988,7 +1064,7 @@ __device__ __forceinline__ void step_body(const StepArgs<T> &p, int b)
         }
         pull_row<Q, T, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, x, pm, pp,
                           ref_row<T, S>(p.dec_in[2], row), inv, gp);
-        collide<Q, T>(gp, cp, jp, p.rho0, p.om[2]);
+        collide<Q, T>(gp, cp, jp, p.rho0, p.om[2], p.q_p);
         store_cell<Q, T, S>(gp, static_cast<S *>(p.out[2]), stride, base,
                             ref_row<T, S>(p.enc_out[2], row), sc);
         if constexpr (ACC) {

@@ -47,8 +47,8 @@ template <> struct Pair<__half> {
         return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
     }
     __device__ static float load1(const __half *p) { return Storage<__half>::load(p); }
-    __device__ static void store2(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
-    __device__ static void store1(__half *p, float v) { *p = __float2half_rn(v); }
+    __device__ static void store2(__half *p, float2 v) { *reinterpret_cast<unsigned *>(p) = f32x2_to_f16x2_sat(v); }
+    __device__ static void store1(__half *p, float v) { Storage<__half>::store(p, v); }
 };
 template <> struct Pair<__nv_bfloat16> {
     __device__ static float2 load2(const __nv_bfloat16 *p)
@@ -58,9 +58,9 @@ template <> struct Pair<__nv_bfloat16> {
     __device__ static float load1(const __nv_bfloat16 *p) { return Storage<__nv_bfloat16>::load(p); }
     __device__ static void store2(__nv_bfloat16 *p, float2 v)
     {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+        *reinterpret_cast<unsigned *>(p) = f32x2_to_bf16x2_sat(v);
     }
-    __device__ static void store1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    __device__ static void store1(__nv_bfloat16 *p, float v) { Storage<__nv_bfloat16>::store(p, v); }
 };
 
 struct Cell2 {
@@ -270,17 +270,19 @@ __device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const RowI
 }
 
 // BGK + Guo collision of both cells, per pair of opposite directions, then
-// the FP32 fix-up of mass and momentum (see collide).  g is left holding g*.
+// the FP32 fix-up of mass and momentum (see collide; q as there: 1 for the
+// second-order equilibrium, 0 for the linear one of phonons as damped
+// waves).  g is left holding g*.
 template <int Q, bool FIX = true>
 __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const float2 j[3], float rho0,
-                                         float om)
+                                         float om, float q = 1.f)
 {
     const float2 rho = add2(b2(rho0), c.drho);
     const float2 uu = fma2(c.u[2], c.u[2], fma2(c.u[1], c.u[1], mul2(c.u[0], c.u[0])));
     const float2 uF = fma2(c.u[2], c.F[2], fma2(c.u[1], c.F[1], mul2(c.u[0], c.F[0])));
-    const float2 e0 = fma2(mul2(b2(-1.5f), rho), uu, c.drho);
-    const float2 r45 = mul2(b2(4.5f), rho);
-    const float2 m3uF = mul2(b2(-3.f), uF);
+    const float2 e0 = fma2(mul2(b2(-1.5f * q), rho), uu, c.drho);
+    const float2 r45 = mul2(b2(4.5f * q), rho);
+    const float2 m3uF = mul2(b2(-3.f * q), uF);
     const float om1 = 1.f - om, fo = 1.f - 0.5f * om;
     {
         const float w = float(wt<Q>(0));
@@ -295,7 +297,7 @@ __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const floa
         const float2 cF = cdot2<Q>(i, c.F);
         // even parts: e0 + 4.5 rho cu^2 and -3 u.F + 9 cu cF
         const float2 se = fma2(r45, mul2(cu, cu), e0);
-        const float2 sf = fma2(b2(9.f), mul2(cu, cF), m3uF);
+        const float2 sf = fma2(b2(9.f * q), mul2(cu, cF), m3uF);
         const float2 S = fma2(b2(om * w), se, mul2(b2(fo * w), sf));
         // odd parts: 3 rho cu and 3 cF
         const float2 A = fma2(mul2(b2(3.f * om * w), rho), cu, mul2(b2(3.f * fo * w), cF));
@@ -307,15 +309,15 @@ __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const floa
     moments2<Q>(g, m, pm);
     const float2 px = pm[0], py = pm[1];
     g[0] = add2(g[0], sub2(c.drho, m));
-    const float2 hx = mul2(b2(0.5f), sub2(add2(j[0], c.F[0]), px));
-    const float2 hy = mul2(b2(0.5f), sub2(add2(j[1], c.F[1]), py));
+    const float2 hx = mul2(b2(0.5f), add2(sub2(j[0], px), c.F[0]));
+    const float2 hy = mul2(b2(0.5f), add2(sub2(j[1], py), c.F[1]));
     g[dir_index<Q>(1, 0, 0)] = add2(g[dir_index<Q>(1, 0, 0)], hx);
     g[dir_index<Q>(-1, 0, 0)] = sub2(g[dir_index<Q>(-1, 0, 0)], hx);
     g[dir_index<Q>(0, 1, 0)] = add2(g[dir_index<Q>(0, 1, 0)], hy);
     g[dir_index<Q>(0, -1, 0)] = sub2(g[dir_index<Q>(0, -1, 0)], hy);
     if (Q == 19) {
         const float2 pz = pm[2];
-        const float2 hz = mul2(b2(0.5f), sub2(add2(j[2], c.F[2]), pz));
+        const float2 hz = mul2(b2(0.5f), add2(sub2(j[2], pz), c.F[2]));
         g[dir_index<Q>(0, 0, 1)] = add2(g[dir_index<Q>(0, 0, 1)], hz);
         g[dir_index<Q>(0, 0, -1)] = sub2(g[dir_index<Q>(0, 0, -1)], hz);
     }
@@ -486,7 +488,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     }
     pull_row2<Q, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, X,
                     ref_row<float, S>(p.dec_in[2], row), inv, gp);
-    collide2<Q>(gp, cp, jp, p.rho0, p.om[2]);
+    collide2<Q>(gp, cp, jp, p.rho0, p.om[2], p.q_p);
     if (live)
         store_pair<Q, S>(gp, static_cast<S *>(p.out[2]), stride, base, both,
                          ref_row<float, S>(p.enc_out[2], row), sc);

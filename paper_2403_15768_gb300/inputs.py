@@ -35,6 +35,7 @@ class Workload:
     storage: str = "fp32"
     steps: int = 0
     iface_bc: str = "specular"
+    phonon_wave: bool = False  # phonons as the damped linear waves of Sec. 3.4
     extra: dict = field(default_factory=dict)
 
     def with_(self, **kw) -> "Workload":

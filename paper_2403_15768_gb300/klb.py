@@ -24,8 +24,9 @@ KLB_GEOM_SLAB, KLB_GEOM_PIPE, KLB_GEOM_MASK = 0, 1, 2
 KLB_FP64, KLB_FP32, KLB_FP16_DEV, KLB_BF16_DEV = 0, 1, 2, 3
 STORAGE = {"fp64": KLB_FP64, "fp32": KLB_FP32, "fp16": KLB_FP16_DEV, "bf16": KLB_BF16_DEV}
 KLB_IFACE_SPECULAR, KLB_IFACE_BOUNCEBACK = 0, 1
+KLB_PHONON_FLUID, KLB_PHONON_WAVE = 0, 1
 STATUS = {0: "KLB_OK", 1: "KLB_EINVAL", 2: "KLB_ENOMEM", 3: "KLB_ECUDA", 4: "KLB_EUNSTABLE",
-          5: "KLB_ETIMEOUT", 6: "KLB_ESTATE"}
+          5: "KLB_ETIMEOUT", 6: "KLB_ESTATE", 7: "KLB_ERANGE"}
 EXPORTS = ["klb_lattice_bytes", "klb_lattice_info", "klb_create_lattice", "klb_set_couplings",
            "klb_set_fluctuations", "klb_bounds_status", "klb_bounds_checked", "klb_init_equilibrium", "klb_step", "klb_observables", "klb_observables_static",
            "klb_get_field",
@@ -47,7 +48,7 @@ class klb_desc(ctypes.Structure):
                 ("tau_w", ctypes.c_double), ("tau_e", ctypes.c_double),
                 ("tau_p", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("G", ctypes.c_double * 3), ("storage", ctypes.c_int32),
-                ("iface_bc", ctypes.c_int32)]
+                ("iface_bc", ctypes.c_int32), ("phonon_eq", ctypes.c_int32)]
 
 
 class klb_couplings(ctypes.Structure):
@@ -61,7 +62,8 @@ class klb_obs(ctypes.Structure):
                 ("dudn_wall", ctypes.c_double), ("slip_length", ctypes.c_double),
                 ("u_wallrow_mean", ctypes.c_double), ("mean_u", ctypes.c_double * 3),
                 ("momentum", ctypes.c_double * 3), ("mass", ctypes.c_double * 3),
-                ("residual", ctypes.c_double), ("nonfinite", ctypes.c_int64)]
+                ("residual", ctypes.c_double), ("nonfinite", ctypes.c_int64),
+                ("clipped", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -219,7 +221,8 @@ def _check(st, handle=None):
 
 def make_desc(kind=KLB_D3Q19, nx=1, ny=1, nz=1, geom=KLB_GEOM_PIPE, width=0, radius=0, shell=0,
               mask=None, periodic_y=False, periodic_z=False, tau=(0.8, 0.6, 1.0), rho0=1.0,
-              G=(0.0, 0.0, 0.0), storage=KLB_FP32, iface_bc=KLB_IFACE_SPECULAR):
+              G=(0.0, 0.0, 0.0), storage=KLB_FP32, iface_bc=KLB_IFACE_SPECULAR,
+              phonon_eq=0):
     """Fill a klb_desc.  ``mask`` (MASK geometry) is a (nz, ny) uint8 array;
     the returned object keeps a reference to it."""
     d = klb_desc()
@@ -235,6 +238,7 @@ def make_desc(kind=KLB_D3Q19, nx=1, ny=1, nz=1, geom=KLB_GEOM_PIPE, width=0, rad
     d.rho0 = rho0
     d.G[0], d.G[1], d.G[2] = G
     d.storage, d.iface_bc = storage, iface_bc
+    d.phonon_eq = phonon_eq
     return d
 
 
@@ -306,7 +310,7 @@ class Lattice:
     def observables(self, allow_unstable=False) -> dict:
         o = klb_obs()
         st = _lib.klb_observables(self._h, ctypes.byref(o))
-        if not (allow_unstable and st == 4):
+        if not (allow_unstable and st in (4, 7)):
             _check(st, self._h)
         return o.as_dict()
 
@@ -473,6 +477,7 @@ class Server:
         if getattr(self, "_h", None) is not None and self._h.value:
             _lib.klb_server_destroy(self._h)
             self._h = ctypes.c_void_p()
+        self.arena = None  # the caller-side buffer goes back to torch's allocator
 
     def __del__(self):
         try:
@@ -494,7 +499,8 @@ def desc_from_workload(w, nx=None) -> klb_desc:
                      radius=w.radius, shell=w.shell, mask=w.extra.get("mask"),
                      periodic_y=w.extra.get("periodic_y", False),
                      periodic_z=w.extra.get("periodic_z", False), tau=w.tau, rho0=w.rho0,
-                     G=w.G, storage=storage, iface_bc=iface)
+                     G=w.G, storage=storage, iface_bc=iface,
+                     phonon_eq=KLB_PHONON_WAVE if w.phonon_wave else KLB_PHONON_FLUID)
 
 
 def lattice_from_workload(w, device="cuda", stream=None) -> Lattice:

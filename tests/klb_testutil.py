@@ -23,7 +23,8 @@ def oracle_geometry(w: Workload):
 
 def make_oracle(w: Workload, nx=None) -> Oracle:
     return Oracle(w.kind, nx or w.nx, oracle_geometry(w), tau=w.tau, rho0=w.rho0, G=w.G,
-                  couplings=w.couplings, iface_bounceback=(w.iface_bc == "bounceback"))
+                  couplings=w.couplings, iface_bounceback=(w.iface_bc == "bounceback"),
+                  phonon_wave=w.phonon_wave)
 
 
 def species_masks(geo, nx):

@@ -69,9 +69,15 @@ def test_long_lattice_reproduces_its_32_cell_slice(w, rel):
     # quantities derived from it are small differences; under 16-bit storage
     # they are compared through the profile they describe (fit_A, the wall-row
     # mean, the flow rate) rather than one by one.
-    keys = PER_SLICE if w.storage != "fp16" else ("flow_rate", "fit_A", "u_wallrow_mean", "residual")
+    keys = PER_SLICE if w.storage != "fp16" else ("flow_rate", "fit_A", "u_wallrow_mean")
     for k in keys:
         assert _close(big[k], small[k], rel), (k, big[k], small[k])
+    # The residual max |u(n) - u(n-1)| is about G = 1e-6 here, a difference of
+    # two velocities whose 16-bit codes hold the drift since the reference
+    # refresh of step 32 (eight steps of about G, stored to 2^-11 of itself):
+    # under FP16 the slices agree on it to a few 1e-3, elsewhere to rel.
+    rel_res = 5e-3 if w.storage == "fp16" else rel
+    assert _close(big["residual"], small["residual"], rel_res), (big["residual"], small["residual"])
     for s in range(3):
         assert _close(big["mean_u"][s], small["mean_u"][s], rel), ("mean_u", s)
         assert _close(big["momentum"][s], r * small["momentum"][s], rel), ("momentum", s)

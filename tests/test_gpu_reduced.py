@@ -2,17 +2,17 @@
 per-row FP32 reference, FP32 arithmetic) against the FP64 oracle, and the
 full-size nanotube against the oracle.
 
-Tolerances come from the bound each case must meet (flow rate and slip
-length within 1% for 16-bit storage, slip length within 0.1% for FP32) and,
-for the velocity fields, from the errors measured on GB300 with a margin of
-about 2x (small pipe after 10^4 steps: FP32 1.2e-6, FP16 4.6e-6, BF16 2.5e-5;
-perturbed start after 2000 steps: FP16 4.2e-4, BF16 2.6e-3; full nanotube
-after 5000 steps: FP32 1.7e-5, FP16 1.6e-5, BF16 2.3e-5).
+Bars: the FP32 velocity field within 1e-5 relative L2 after 10^4 steps and
+the slip length within 0.1%; flow rate and slip length within 1% for 16-bit
+storage.  Where no bar is stated (16-bit velocity fields, the small cases),
+tolerances are the errors measured on GB300 with a margin of about 2x
+(small pipe after 10^4 steps: FP16 4.6e-6, BF16 2.5e-5; perturbed start
+after 2000 steps: FP16 4.2e-4, BF16 2.6e-3).
 """
 import numpy as np
 import pytest
 
-from klb_testutil import make_oracle, rel_l2, species_masks
+from klb_testutil import make_oracle, oracle_geometry, rel_l2, species_masks
 from oracle import observables_from_fields
 from paper_2403_15768_gb300 import inputs, klb
 
@@ -79,8 +79,8 @@ def test_reduced_d2q9_slab_10k(storage, tol):
 
 
 _FULL = {}
-# the bars: 0.1% for FP32, 1% for 16-bit storage (measured on GB300: at most
-# 6.4e-5 for every storage)
+FULL_STEPS = 10_000
+# the bars: 0.1% for FP32, 1% for 16-bit storage
 PER_OBS_TOL = {"fp32": 1e-3, "fp16": 1e-2, "bf16": 1e-2}
 
 
@@ -92,39 +92,106 @@ def _full_oracle():
         w = inputs.PIPE_D3Q19_FP32
         o = make_oracle(w, nx=1)
         o.init_equilibrium()
-        o.step(5000)
+        o.step(FULL_STEPS)
         f = o.observe()
         _FULL["geo"], _FULL["f"] = o.geo, f
         _FULL["obs"] = observables_from_fields(o.geo, 1, w.rho0, f)
     return _FULL["geo"], _FULL["f"], _FULL["obs"]
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 3.5e-5), ("fp16", 3.5e-5), ("bf16", 5e-5)])
-def test_full_nanotube_5000_steps_against_oracle(storage, tol):
-    """The 512x128x128 nanotube in the benchmark's launch configuration, 5000
-    steps from rest, against the oracle: slip length within 0.1% (FP32) and
-    flow rate within 1e-4; velocity field within the stated tolerance."""
+def _per_observable(ob, ob_o):
+    keys = ("flow_rate", "slip_length", "u_slip", "dudn_wall", "u_wallrow_mean")
+    err = {k: abs(ob[k] / ob_o[k] - 1.0) for k in keys}
+    err.update({f"mean_u[{s}]": abs(ob["mean_u"][s] / ob_o["mean_u"][s] - 1.0) for s in range(3)})
+    return err
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16", 1e-5), ("bf16", 1e-5)])
+def test_full_nanotube_10k_steps_against_oracle(storage, tol):
+    """The 512x128x128 nanotube in the benchmark's launch configuration, 10^4
+    steps from rest, against the oracle: FP32 velocity fields within 1e-5
+    relative L2 and slip length within 0.1%; every observable of the
+    slip-length study within its bar."""
     import torch
 
     geo, f, ob_o = _full_oracle()
     w = inputs.PIPE_D3Q19_FP32.with_(storage=storage)
     lat = klb.lattice_from_workload(w)
-    lat.step(5000)
+    lat.step(FULL_STEPS)
     _, ug = lat.get_field()
     ob = lat.observables()
     m = species_masks(geo, 1)
+    errs = []
     for s in range(3):
         assert np.abs(ug[s] - ug[s][..., :1]).max() == 0.0  # every x plane identical
-        assert rel_l2(ug[s][..., :1][:, m[s]], f["u"][s][:, m[s]]) <= tol
-    assert ob["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
-    assert ob["flow_rate"] == pytest.approx(ob_o["flow_rate"], rel=1e-4)  # both per unit length
-    # every observable the paper's slip-length study needs, each against the oracle
-    per_obs = {k: abs(ob[k] / ob_o[k] - 1.0) for k in ("u_slip", "dudn_wall", "u_wallrow_mean")}
-    per_obs.update({f"mean_u[{s}]": abs(ob["mean_u"][s] / ob_o["mean_u"][s] - 1.0) for s in range(3)})
-    print(storage, per_obs)
+        errs.append(rel_l2(ug[s][..., :1][:, m[s]], f["u"][s][:, m[s]]))
+    per_obs = _per_observable(ob, ob_o)
+    print(storage, "rel-L2", errs, per_obs)
+    assert max(errs) <= tol, errs
+    assert per_obs["slip_length"] <= PER_OBS_TOL[storage]
+    assert per_obs["flow_rate"] <= 1e-4
     assert max(per_obs.values()) <= PER_OBS_TOL[storage], per_obs
+    assert ob["nonfinite"] == 0 and ob["clipped"] == 0
     del lat
     torch.cuda.empty_cache()
+
+
+_SUB = {}
+
+
+def _sub_oracle():
+    """The oracle's 128x64x64 subcase after 5000 steps from a perturbed,
+    x-varying start, as stored by tests/golden/make_pipe_sub_oracle.py (the
+    oracle needs about ten minutes of one core for it)."""
+    if not _SUB:
+        import json
+        import os
+
+        z = np.load(os.path.join(os.path.dirname(__file__), "golden", "pipe_sub_perturbed_5000.npz"))
+        _SUB.update(steps=int(z["steps"]), seed=int(z["seed"]), eps=float(z["eps"]),
+                    planes=[int(v) for v in z["planes"]], u=z["u"], drho=z["drho"],
+                    obs=json.loads(str(z["observables"])))
+    return _SUB
+
+
+# the x-varying part (differences between the stored planes, about 3e-4 of
+# the flow at step 5000) carries the 16-bit rounding of the stored
+# differences; measured on GB300 2.2x below these: FP32 1.5e-4, FP16 1.7e-3,
+# BF16 1.0e-1 (BF16 keeps 8 bits of a difference that is itself small)
+XVAR_TOL = {"fp32": 3e-4, "fp16": 4e-3, "bf16": 0.2}
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16", 2e-5), ("bf16", 2e-3)])
+def test_subcase_perturbed_start_against_oracle(storage, tol):
+    """The 128x64x64 nanotube subcase (radius 24, shell 3) from a seeded,
+    x-varying perturbed start, 5000 steps, against the FP64 oracle: velocity
+    fields of every species on the stored x planes (relative L2), and every
+    observable; flow rate and slip length within 1% for 16-bit storage,
+    0.1% for FP32."""
+    ref = _sub_oracle()
+    w = inputs.PIPE_D3Q19_SUB.with_(storage=storage)
+    lat = klb.lattice_from_workload(w)
+    d, u = inputs.perturbation(w, ref["seed"], ref["eps"])
+    lat.init_equilibrium(d, u)
+    lat.step(ref["steps"])
+    _, ug = lat.get_field()
+    ob = lat.observables()
+    geo = oracle_geometry(w)
+    m = species_masks(geo, len(ref["planes"]))
+    ug = ug[..., ref["planes"]]
+    errs = [rel_l2(ug[s][:, m[s]], ref["u"][s][:, m[s]]) for s in range(3)]
+    # the start really is x-varying, and still is at the end
+    assert np.abs(ref["u"][0, 0, ..., 0] - ref["u"][0, 0, ..., 1]).max() > 1e-4 * np.abs(ref["u"][0, 0]).max()
+    # the x-varying part alone: differences between the stored planes
+    dx = [rel_l2((ug[s][..., 1:] - ug[s][..., :1])[:, m[s][..., 1:]],
+                 (ref["u"][s][..., 1:] - ref["u"][s][..., :1])[:, m[s][..., 1:]]) for s in range(3)]
+    per_obs = _per_observable(ob, ref["obs"])
+    print(storage, "rel-L2", errs, "x-varying part", dx, per_obs)
+    assert max(errs) <= tol, errs
+    assert max(dx) <= XVAR_TOL[storage], dx
+    bar = 1e-3 if storage == "fp32" else 1e-2
+    assert per_obs["flow_rate"] <= bar and per_obs["slip_length"] <= bar, per_obs
+    assert ob["nonfinite"] == 0 and ob["clipped"] == 0
 
 
 @pytest.mark.parametrize("storage", ["fp16", "bf16"])
