@@ -219,6 +219,12 @@ cudaError_t refresh_refs(const klb_lattice *L, int gen)
 
 int nblocks(const klb_lattice *L) { return L->plan.nblocks_w + L->plan.nblocks_s; }
 
+// Grid of the observation pass: with FP32 arithmetic two cells per thread on
+// the step kernel's grid (at most nblocks(L) blocks, the size of the partial
+// sums region), with FP64 one cell per thread.
+int obs_blocks(const klb_lattice *L) { return L->desc.storage == KLB_FP64 ? nblocks(L) : L->plan.snblocks; }
+int obs_bx(const klb_lattice *L) { return L->desc.storage == KLB_FP64 ? L->plan.bx : L->plan.sbx; }
+
 // Species field index helpers: row class and row count of species s.
 int cls_of(int s) { return s == 0 ? kFluid : kSolid; }
 
@@ -516,10 +522,10 @@ klb_status klb_step(klb_lattice *L, int64_t nsteps)
 cudaError_t klb::observe_enqueue(klb_lattice *L, double *host_sums)
 {
     cudaError_t e = with_args(L, [&](void *a) {
-        return launch(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L), L->plan.bx, L->stream);
+        return launch(L->geo.Q, L->desc.storage, a, kModeObserve, obs_blocks(L), obs_bx(L), L->stream);
     });
     if (e == cudaSuccess)
-        e = launch_finalize((const double *)dev(L, L->plan.partials), nblocks(L), (double *)dev(L, L->plan.sums),
+        e = launch_finalize((const double *)dev(L, L->plan.partials), obs_blocks(L), (double *)dev(L, L->plan.sums),
                             L->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_sums, dev(L, L->plan.sums), sizeof(double) * kNumSums, cudaMemcpyDeviceToHost,
@@ -538,10 +544,10 @@ klb_status klb_observables(klb_lattice *L, klb_obs *out)
 {
     if (!L || !out) return fail(L, KLB_EINVAL, "null argument");
     KLB_CUDA(L, with_args(L, [&](void *a) {
-                 return launch(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L),
-                                    L->plan.bx, L->stream);
+                 return launch(L->geo.Q, L->desc.storage, a, kModeObserve, obs_blocks(L),
+                                    obs_bx(L), L->stream);
              }));
-    KLB_CUDA(L, launch_finalize((const double *)dev(L, L->plan.partials), nblocks(L),
+    KLB_CUDA(L, launch_finalize((const double *)dev(L, L->plan.partials), obs_blocks(L),
                                 (double *)dev(L, L->plan.sums), L->stream));
     double S[kNumSums];
     KLB_CUDA(L, cudaMemcpyAsync(S, dev(L, L->plan.sums), sizeof S, cudaMemcpyDeviceToHost,
@@ -557,9 +563,9 @@ klb_status klb_observables_static(klb_lattice *L, klb_obs *out)
     double *partials = nullptr, *sums = nullptr;
     size_t max_blocks = 0;
     KLB_CUDA(L, static_scratch(&partials, &sums, &max_blocks));
-    if ((size_t)nblocks(L) > max_blocks)
+    if ((size_t)obs_blocks(L) > max_blocks)
         return fail(L, KLB_EINVAL,
-                    "observation pass needs " + std::to_string(nblocks(L)) +
+                    "observation pass needs " + std::to_string(obs_blocks(L)) +
                         " blocks, more than the static scratch holds (KLB_STATIC_MAX_BLOCKS = " +
                         std::to_string(max_blocks) + ")");
     KLB_CUDA(L, with_args(L, [&](void *a) {
@@ -567,10 +573,10 @@ klb_status klb_observables_static(klb_lattice *L, klb_obs *out)
                      static_cast<StepArgs<double> *>(a)->partials = partials;
                  else
                      static_cast<StepArgs<float> *>(a)->partials = partials;
-                 return launch(L->geo.Q, L->desc.storage, a, kModeObserve, nblocks(L),
-                                    L->plan.bx, L->stream);
+                 return launch(L->geo.Q, L->desc.storage, a, kModeObserve, obs_blocks(L),
+                                    obs_bx(L), L->stream);
              }));
-    KLB_CUDA(L, launch_finalize(partials, nblocks(L), sums, L->stream));
+    KLB_CUDA(L, launch_finalize(partials, obs_blocks(L), sums, L->stream));
     double S[kNumSums];
     KLB_CUDA(L, cudaMemcpyAsync(S, sums, sizeof S, cudaMemcpyDeviceToHost, L->stream));
     klb_status st = sync(L);

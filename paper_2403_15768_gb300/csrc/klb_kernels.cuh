@@ -513,7 +513,7 @@ __device__ __forceinline__ double warp_max(double v)
 }
 
 // Block sums of the observation pass (one row chunk per block, so the row
-// class and flags are block-uniform).  Only the sums that can be non-zero
+// class and flags are block-uniform; ncell = the thread's live cells).  Only the sums that can be non-zero
 // for the block's class run a warp reduction (FP64 throughput on GB300 is a
 // small fraction of FP32); the slip-fit count and distance moments and the wall-row count
 // follow from the number of live cells and the row's d^2, the fit and
@@ -522,7 +522,7 @@ __device__ __forceinline__ double warp_max(double v)
 // predicate counts.  Each entry equals what a reduction of the per-cell
 // values gives.
 __device__ inline void observe_reduce_store(const double (&s)[kNumSums], bool water, int flags, double d2,
-                                            bool live, double *out)
+                                            int ncell, double *out)
 {
     __shared__ double red[kNumSums][kBlockX / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -533,11 +533,14 @@ __device__ inline void observe_reduce_store(const double (&s)[kNumSums], bool wa
                     (fit ? (1u << kSumFitUD2) : 0u)
               : (1u << kSumUxE) | (1u << kSumUxP) | (1u << kSumMomE) | (1u << kSumMomP) | (1u << kSumMassE) |
                     (1u << kSumMassP) | (1u << kSumResidual);
-    const int cnt = __syncthreads_count(live);
-    const int nonfinite =
-        __syncthreads_count(s[kSumNonfinite] >= 1.0) + __syncthreads_count(s[kSumNonfinite] >= 2.0);
-    const int clipped =
-        __syncthreads_count(s[kSumClipped] >= 1.0) + __syncthreads_count(s[kSumClipped] >= 2.0);
+    const int cnt = __syncthreads_count(ncell >= 1) + __syncthreads_count(ncell >= 2);  // live cells
+    // per-thread counts of up to four species-cells (two cells of two species)
+    auto count4 = [](double v) {
+        return __syncthreads_count(v >= 1.0) + __syncthreads_count(v >= 2.0) + __syncthreads_count(v >= 3.0) +
+               __syncthreads_count(v >= 4.0);
+    };
+    const int nonfinite = count4(s[kSumNonfinite]);
+    const int clipped = count4(s[kSumClipped]);
 #pragma unroll
     for (int k = 0; k < kNumSums; ++k) {
         if (!((sel >> k) & 1u)) continue;
@@ -721,7 +724,7 @@ __global__ void __launch_bounds__(kBlockX, (sizeof(T) == 4 ? 8 : 1)) k_lattice(c
     }
     if (MODE == kModeObserve) {
         const RowInfo &Rb = p.rows[water ? kFluid : kSolid][row];
-        observe_reduce_store(s, water, water ? Rb.flags : 0, (double)Rb.d2, live,
+        observe_reduce_store(s, water, water ? Rb.flags : 0, (double)Rb.d2, live ? 1 : 0,
                              p.partials + (size_t)b * kNumSums);
     }
 }
@@ -1224,7 +1227,12 @@ cudaError_t launch_q(const void *args, int mode, int nblocks, int bx, cudaStream
         else
             return cudaErrorInvalidValue;
     case kModeObserve:
-        k_lattice<Q, T, S, kModeObserve><<<nblocks, bx, 0, s>>>(a);
+        // FP32 arithmetic: two cells per thread on the step grid (the caller
+        // passes its blocks and width); FP64: one cell per thread
+        if constexpr (sizeof(T) == 4)
+            k_observe2<Q, S><<<nblocks, bx, 0, s>>>(a);
+        else
+            k_lattice<Q, T, S, kModeObserve><<<nblocks, bx, 0, s>>>(a);
         break;
     case kModeField:
         k_lattice<Q, T, S, kModeField><<<nblocks, bx, 0, s>>>(a);

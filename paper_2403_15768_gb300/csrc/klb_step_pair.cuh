@@ -194,8 +194,11 @@ __device__ __forceinline__ float2 lagged2(const float *U1, const float *U2, int 
 
 __device__ __forceinline__ float2 rcp2(float2 r) { return make_float2(1.f / r.x, 1.f / r.y); }
 
+// Uw1, Uw2 / Us1, Us2: the lagged velocities of the two steps before the
+// time level of g (water / solid), as in water_math.
 template <int Q>
-__device__ __forceinline__ void water_math2(const StepArgs<float> &p, const RowInfo &R, int x0,
+__device__ __forceinline__ void water_math2(const StepArgs<float> &p, const float *Uw1, const float *Uw2,
+                                            const float *Us1, const float *Us2, const RowInfo &R, int x0,
                                             const float2 g[Q], Cell2 &c, float2 j[3])
 {
     moments2<Q>(g, c.drho, j);
@@ -206,7 +209,6 @@ __device__ __forceinline__ void water_math2(const StepArgs<float> &p, const RowI
     if (slot >= 0) {
         const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
         const int nface = R.nface;
-        const float *Uw1 = p.U1[kFluid], *Uw2 = p.U2[kFluid], *Us1 = p.U1[kSolid], *Us2 = p.U2[kSolid];
         for (int a = 0; a < 3; ++a) {
             const float2 uw = lagged2(Uw1, Uw2, (a * ns_w + slot) * nxp + x0);
             float2 f = b2(0.f);
@@ -225,7 +227,8 @@ __device__ __forceinline__ void water_math2(const StepArgs<float> &p, const RowI
 }
 
 template <int Q>
-__device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const RowInfo &R, int x0,
+__device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const float *Uw1, const float *Uw2,
+                                            const float *Us1, const float *Us2, const RowInfo &R, int x0,
                                             const float2 ge[Q], const float2 gp[Q], Cell2 &ce,
                                             Cell2 &cp, float2 je[3], float2 jp[3])
 {
@@ -236,7 +239,6 @@ __device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const RowI
     if (slot >= 0) {
         const int ns_w = p.n_slots[kFluid], ns_s = p.n_slots[kSolid], nxp = p.nxp;
         const int nface = R.nface;
-        const float *Uw1 = p.U1[kFluid], *Uw2 = p.U2[kFluid], *Us1 = p.U1[kSolid], *Us2 = p.U2[kSolid];
         for (int a = 0; a < 3; ++a) {
             const float2 ue = lagged2(Us1, Us2, (a * ns_s + slot) * nxp + x0);
             const float2 up = lagged2(Us1, Us2, ((a + 3) * ns_s + slot) * nxp + x0);
@@ -436,7 +438,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
         Cell2 c;
         pull_row2<Q, S>(static_cast<const S *>(p.in[0]), src, xm, xp, xbounce, X,
                         ref_row<float, S>(p.dec_in[0], row), inv, g);
-        water_math2<Q>(p, R, X.x0, g, c, j);
+        water_math2<Q>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, X.x0, g, c, j);
         if (q5.y >= 0 && live) {
             const int ns = p.n_slots[kFluid];
             for (int a = 0; a < 3; ++a) store_u2(p.U0[kFluid] + (a * ns + q5.y) * nxp + X.x0, c.u[a], both);
@@ -468,7 +470,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
                     ref_row<float, S>(p.dec_in[1], row), inv, ge);
     pull_row2<Q, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, X,
                     ref_row<float, S>(p.dec_in[2], row), inv, gp);
-    solid_math2<Q>(p, R, X.x0, ge, gp, ce, cp, je, jp);
+    solid_math2<Q>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, X.x0, ge, gp, ce, cp, je, jp);
     if (q5.y >= 0 && live) {
         const int ns = p.n_slots[kSolid];
         for (int a = 0; a < 3; ++a) {
@@ -497,6 +499,138 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
         for (int i = 0; i < Q; ++i) acc[Q + i] = (live ? gp[i].x : 0.f) + (both ? gp[i].y : 0.f);
         segment_xsum<2, 2 * Q>(acc, p.acc, seg, 2 * Q);
     }
+}
+
+// Observation pass with two cells per thread (FP32 arithmetic), on the step
+// kernel's grid (solid blocks first): the velocities of the current step
+// (lagged velocities U1, U2) and, for the residual, of the previous one (U2,
+// U3), from the same pulls and arithmetic as the step, reduced per block in
+// FP64 into the partial sums of the observation (observe_reduce_store).
+__device__ __forceinline__ bool finite2(const Cell2 &c, int e)
+{
+    const float v[4] = {e ? c.drho.y : c.drho.x, e ? c.u[0].y : c.u[0].x, e ? c.u[1].y : c.u[1].x,
+                        e ? c.u[2].y : c.u[2].x};
+    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]) && isfinite(v[3]);
+}
+
+template <int Q, typename S>
+__global__ void __launch_bounds__(kBlockX, 4) k_observe2(const StepArgs<float> p)
+{
+    const int b = blockIdx.x;
+    const int nsb = p.n_rows[kSolid] * p.snchunk_s;
+    const bool water = b >= nsb;
+    const int bb = water ? b - nsb : b;
+    const int nch = water ? p.snchunk_w : p.snchunk_s;
+    int row = bb / nch;
+    const int x_first = 2 * ((bb - row * nch) * (int)blockDim.x + (int)threadIdx.x);
+    bool live = x_first < p.nx;
+    if constexpr (KLB_BOUNDS) {
+        if (live && !row_indices_ok<Q>(p, water, row, 0, x_first + 1)) {
+            live = false;
+            row = 0;
+        }
+    }
+    const bool both = live && x_first + 1 < p.nx;
+    double s[kNumSums];
+#pragma unroll
+    for (int k = 0; k < kNumSums; ++k) s[k] = 0.0;
+    const RowInfo &R = p.rows[water ? kFluid : kSolid][row];
+    if (live) {
+        Cols X;
+        X.x0 = x_first;
+        X.pm_a = X.x0 == 0 ? p.nx - 1 : X.x0 - 1;
+        X.pp_a = X.x0 + 1 >= p.nx ? 0 : X.x0 + 1;
+        X.pp_b = X.x0 + 2 >= p.nx ? 0 : X.x0 + 2;
+        const float inv = p.inv_scale;
+        const int4 *t4 = reinterpret_cast<const int4 *>(&R);
+        int src[20];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            const int4 q = __ldg(t4 + v);
+            src[4 * v] = q.x;
+            src[4 * v + 1] = q.y;
+            src[4 * v + 2] = q.z;
+            src[4 * v + 3] = q.w;
+        }
+        const uint32_t xm = (uint32_t)src[19];
+        const int4 q5 = __ldg(t4 + 5);
+        const int4 q7 = __ldg(t4 + 7);
+        const uint32_t xp = (uint32_t)q5.x;
+        const bool xbounce = (q7.x & kXBounce) != 0;
+        // the previous step first (for the residual), keeping only its u_x,
+        // so that the current step's values and sums are live alone
+        if (water) {
+            float2 g[Q], j[3];
+            float2 uq = b2(0.f);
+            if (p.residual_valid) {
+                Cell2 cq;
+                pull_row2<Q, S>(static_cast<const S *>(p.in_prev[0]), src, xm, xp, xbounce, X,
+                                ref_row<float, S>(p.dec_prev[0], row), inv, g);
+                water_math2<Q>(p, p.U2[kFluid], p.U3[kFluid], p.U2[kSolid], p.U3[kSolid], R, X.x0, g, cq, j);
+                uq = cq.u[0];
+            }
+            Cell2 c;
+            pull_row2<Q, S>(static_cast<const S *>(p.in[0]), src, xm, xp, xbounce, X,
+                            ref_row<float, S>(p.dec_in[0], row), inv, g);
+            water_math2<Q>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, X.x0, g, c, j);
+            const double u0 = c.u[0].x, u1 = both ? (double)c.u[0].y : 0.0;
+            s[kSumUxFluid] = u0 + u1;
+            // the second cell of an odd row's last pair lies in the padding:
+            // none of its values enters a sum
+            s[kSumMomW] = (double)(p.rho0 + c.drho.x) * u0 + (both ? (double)(p.rho0 + c.drho.y) * u1 : 0.0);
+            s[kSumMassW] = (double)c.drho.x + (both ? (double)c.drho.y : 0.0);
+            s[kSumNonfinite] = (finite2(c, 0) ? 0.0 : 1.0) + (both && !finite2(c, 1) ? 1.0 : 0.0);
+            const S *in0 = static_cast<const S *>(p.in[0]);
+            s[kSumClipped] = (clipped_cell<Q, S>(in0, R, X.x0, X.pm_a, X.pp_a) ? 1.0 : 0.0) +
+                             (both && clipped_cell<Q, S>(in0, R, X.x0 + 1, X.x0, X.pp_b) ? 1.0 : 0.0);
+            if (R.flags & kFitRow) s[kSumFitUD2] = (u0 + u1) * (double)R.d2;
+            if (p.residual_valid)
+                s[kSumResidual] = fmax(fabs(u0 - (double)uq.x), both ? fabs(u1 - (double)uq.y) : 0.0);
+        } else {
+            float2 ge[Q], gp[Q], je[3], jp[3];
+            float2 eq = b2(0.f), pq = b2(0.f);
+            if (p.residual_valid) {
+                Cell2 qe, qp;
+                pull_row2<Q, S>(static_cast<const S *>(p.in_prev[1]), src, xm, xp, xbounce, X,
+                                ref_row<float, S>(p.dec_prev[1], row), inv, ge);
+                pull_row2<Q, S>(static_cast<const S *>(p.in_prev[2]), src, xm, xp, xbounce, X,
+                                ref_row<float, S>(p.dec_prev[2], row), inv, gp);
+                solid_math2<Q>(p, p.U2[kFluid], p.U3[kFluid], p.U2[kSolid], p.U3[kSolid], R, X.x0, ge, gp, qe, qp,
+                               je, jp);
+                eq = qe.u[0];
+                pq = qp.u[0];
+            }
+            Cell2 ce, cp;
+            pull_row2<Q, S>(static_cast<const S *>(p.in[1]), src, xm, xp, xbounce, X,
+                            ref_row<float, S>(p.dec_in[1], row), inv, ge);
+            pull_row2<Q, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, X,
+                            ref_row<float, S>(p.dec_in[2], row), inv, gp);
+            solid_math2<Q>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, X.x0, ge, gp, ce, cp, je,
+                           jp);
+            const double e0 = ce.u[0].x, e1 = both ? (double)ce.u[0].y : 0.0;
+            const double p0 = cp.u[0].x, p1 = both ? (double)cp.u[0].y : 0.0;
+            s[kSumUxE] = e0 + e1;
+            s[kSumUxP] = p0 + p1;
+            s[kSumMomE] = (double)(p.rho0 + ce.drho.x) * e0 + (both ? (double)(p.rho0 + ce.drho.y) * e1 : 0.0);
+            s[kSumMomP] = (double)(p.rho0 + cp.drho.x) * p0 + (both ? (double)(p.rho0 + cp.drho.y) * p1 : 0.0);
+            s[kSumMassE] = (double)ce.drho.x + (both ? (double)ce.drho.y : 0.0);
+            s[kSumMassP] = (double)cp.drho.x + (both ? (double)cp.drho.y : 0.0);
+            s[kSumNonfinite] = (finite2(ce, 0) ? 0.0 : 1.0) + (finite2(cp, 0) ? 0.0 : 1.0) +
+                               (both && !finite2(ce, 1) ? 1.0 : 0.0) + (both && !finite2(cp, 1) ? 1.0 : 0.0);
+            const S *in1 = static_cast<const S *>(p.in[1]), *in2 = static_cast<const S *>(p.in[2]);
+            s[kSumClipped] = (clipped_cell<Q, S>(in1, R, X.x0, X.pm_a, X.pp_a) ? 1.0 : 0.0) +
+                             (clipped_cell<Q, S>(in2, R, X.x0, X.pm_a, X.pp_a) ? 1.0 : 0.0) +
+                             (both && clipped_cell<Q, S>(in1, R, X.x0 + 1, X.x0, X.pp_b) ? 1.0 : 0.0) +
+                             (both && clipped_cell<Q, S>(in2, R, X.x0 + 1, X.x0, X.pp_b) ? 1.0 : 0.0);
+            if (p.residual_valid) {
+                double r = fmax(fabs(e0 - (double)eq.x), fabs(p0 - (double)pq.x));
+                if (both) r = fmax(r, fmax(fabs(e1 - (double)eq.y), fabs(p1 - (double)pq.y)));
+                s[kSumResidual] = r;
+            }
+        }
+    }
+    observe_reduce_store(s, water, water ? R.flags : 0, (double)R.d2, live ? (both ? 2 : 1) : 0,
+                         p.partials + (size_t)b * kNumSums);
 }
 
 }  // namespace klb
