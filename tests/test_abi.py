@@ -79,6 +79,36 @@ def test_invalid_descriptions_are_rejected(change, msg):
     assert e.value.status == 1 and msg in str(e.value)
 
 
+def test_phonon_equilibrium_option_is_validated():
+    """klb_desc.phonon_eq accepts the default second-order equilibrium (0) and
+    the damped-wave variant of Sec. 3.4 (1), with the same sizes; any other
+    value is rejected on the host."""
+    w = inputs.PIPE_D3Q19_SUB
+    d0 = klb.desc_from_workload(w)
+    d1 = klb.desc_from_workload(w.with_(phonon_wave=True))
+    assert d0.phonon_eq == klb.KLB_PHONON_FLUID and d1.phonon_eq == klb.KLB_PHONON_WAVE
+    assert klb.klb_lattice_bytes(d0) == klb.klb_lattice_bytes(d1) > 0
+    d1.phonon_eq = 2
+    assert klb.klb_lattice_bytes(d1) == 0
+    with pytest.raises(klb.KLBError) as e:
+        klb.klb_lattice_info(d1)
+    assert e.value.status == 1 and "phonon_eq" in str(e.value)
+
+
+def test_status_codes_match_the_header():
+    """The binding's status names follow include/klb.h, including the
+    saturated 16-bit range (KLB_ERANGE)."""
+    import re
+
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "klb.h")).read()
+    body = hdr[hdr.index("typedef enum {\n    KLB_OK"):hdr.index("} klb_status;")]
+    codes = {name: int(v) for name, v in re.findall(r"(KLB_[A-Z]+) = (\d+)", body)}
+    for v, name in klb.STATUS.items():
+        assert codes[name] == v, name
+    assert codes["KLB_ERANGE"] == 7
+
+
 def test_mask_geometry_and_empty_species():
     mask = np.array([[2, 1, 1, 2]], np.uint8)
     d = klb.make_desc(kind=9, nx=4, ny=4, nz=1, geom=klb.KLB_GEOM_MASK, mask=mask,
