@@ -1,8 +1,9 @@
 """The benchmark's JSON line keeps its contract: one line with the metric,
 the device-timed value, the end-to-end value through the C ABI with its
 host<->device bytes, the step kernel's roofline against the measured peak,
-the timed oracle baseline, the clocks seen during the timed region and the
-number of library kernels launched."""
+the timed oracle baseline, the clocks seen during the timed region, the
+number of library kernels launched, and the FP32-vs-16-bit and serving
+blocks."""
 import json
 import os
 import subprocess
@@ -41,3 +42,14 @@ def test_default_bench_line():
     assert d["gpu_launches"] == 6 * (100 + 2)
     clk = d["clocks"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(clk)
+    # FP32 against 16-bit storage on the 768x192x192 nanotube, and a short
+    # serving trace per storage (the metric's FP32-vs-FP16 and p50/p99 parts)
+    pr = d["precision"]
+    for st in ("fp32", "fp16", "bf16"):
+        assert pr[st]["launch_ms"] > 0 and 0.1 < pr[st]["roofline_frac"] < 1.2
+        assert pr[st]["bytes_per_launch"] == 19_184_640 * 2 * 19 * (4 if st == "fp32" else 2)
+    assert abs(pr["fp16_over_fp32"] - pr["fp16"]["mlups"] / pr["fp32"]["mlups"]) < 1e-9
+    sv = d["serving"]
+    for st in ("fp32", "fp16"):
+        assert sv[st]["mlups"] > 0 and 0 < sv[st]["p50_s"] <= sv[st]["p99_s"]
+        assert sum(sv[st]["status"].values()) == sv["requests"]
