@@ -283,18 +283,19 @@ def _serving_block(dev, n=12):
     """A short seeded trace of the request loop per storage (n requests of
     the Poisson stream, 50 per second, seed 0, cells log-uniform in
     [32^3, 512 x 128 x 128], run to the residual tolerance or 2 x 10^4
-    steps): p50 / p99 time to solution and aggregate MLUPS."""
+    steps; the batch block width autotuned at every re-forming of the
+    batch): p50 / p99 time to solution and aggregate MLUPS."""
     import torch
 
     from paper_2403_15768_gb300 import inputs, klb, serving
 
-    out = {"requests": n, "rate_per_s": 50.0, "max_steps": 20000, "check_every": 100}
+    out = {"requests": n, "rate_per_s": 50.0, "max_steps": 20000, "check_every": 100, "autotune_steps": 5}
     for storage in ("fp32", "fp16"):
         tol = 1e-9 if storage == "fp32" else 1e-7
         stream = torch.cuda.Stream(dev)
         with torch.cuda.stream(stream):
             srv = klb.Server(40 * 10 ** 9, storage=storage, check_every=100, max_resident=128,
-                             device=dev, stream=stream)
+                             autotune_steps=5, device=dev, stream=stream)
             serving.replay(srv, inputs.request_stream(2, rate=50.0, seed=1000, storage=storage,
                                                       max_cells=64 ** 3), tol=tol, max_steps=1000)
             run = serving.replay(srv, inputs.request_stream(n, rate=50.0, seed=0, storage=storage),
@@ -551,8 +552,8 @@ def run_serving(args):
     arena = 150 * 10 ** 9
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        srv = klb.Server(arena, storage=storage, check_every=100, max_resident=128, device=dev,
-                         stream=stream)
+        srv = klb.Server(arena, storage=storage, check_every=100, max_resident=128, autotune_steps=5,
+                         device=dev, stream=stream)
         if args.warmup:
             warm = inputs.request_stream(args.warmup, rate=50.0, seed=1000 + rank, storage=storage,
                                          max_cells=64 ** 3)
@@ -576,7 +577,8 @@ def run_serving(args):
         "config": {"workload": f"Poisson request stream, {args.rate:g}/s, seed = rank, {storage}",
                    "rate_per_s": args.rate,
                    "storage": storage, "requests": args.steps, "tol": tol, "max_steps": max_steps,
-                   "check_every": 100, "arena_bytes": arena, "parallelism": f"replicas x{world}"},
+                   "check_every": 100, "autotune_steps": 5, "arena_bytes": arena,
+                   "parallelism": f"replicas x{world}"},
         "serving": {k: summ[k] for k in ("p50_s", "p99_s", "mean_s", "wait_p50_s", "wait_p99_s",
                                           "status", "makespan_s")},
         "roofline": None,
