@@ -294,8 +294,9 @@ klb_status klb_observables(klb_lattice *lat, klb_obs *out);
  * allocating library routine is called.
  *
  * - Lattices whose observation pass needs more than KLB_STATIC_MAX_BLOCKS
- *   thread blocks (one per 128 x positions of each cross-section cell) are
- *   rejected with KLB_EINVAL and a message naming the limit.
+ *   thread blocks (per cross-section cell, one per 256 x positions with
+ *   FP32 arithmetic, one per 128 with FP64 storage) are rejected with
+ *   KLB_EINVAL and a message naming the limit.
  * - The first call on a device looks up the device address of the array
  *   (once per device, with that device current); make that first call before
  *   any stream capture.

@@ -190,7 +190,7 @@ cudaError_t launch_batch(int Q, int storage, const void *table, const int *prefi
 // storage (the layout klb_batch_create uses).
 size_t batch_table_bytes(int storage, int n);
 
-// Observation pass of a lattice enqueued on its stream, its 18 sums copied
+// Observation pass of a lattice enqueued on its stream, its kNumSums sums copied
 // to host_sums (pinned host memory; valid after the stream synchronises),
 // and the observables computed from them (klb_observables in two halves).
 cudaError_t observe_enqueue(klb_lattice *L, double *host_sums);
