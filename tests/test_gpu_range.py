@@ -80,3 +80,19 @@ def test_bf16_and_fp32_hold_the_same_perturbation():
         lat.init_equilibrium(_alternating_density(w, 0.3), None)
         ob = lat.observables()
         assert ob["clipped"] == 0 and ob["nonfinite"] == 0
+
+
+def test_fp16_clipping_is_counted_per_species_cell():
+    """The count is per species-cell: a +-0.3 alternation of the electron
+    and phonon densities puts one saturated population in every solid cell
+    of each species (2 x the solid cells), and water stays clear."""
+    w = PIPE.with_(storage="fp16")
+    lat = klb.lattice_from_workload(w)
+    d = np.zeros((3, w.nz, w.ny, w.nx))
+    alt = 0.3 * np.where(np.arange(w.nx) % 2 == 0, 1.0, -1.0)
+    d[1] = alt
+    d[2] = alt
+    lat.init_equilibrium(d, None)
+    ob = lat.observables(allow_unstable=True)
+    assert ob["clipped"] == lat.species_cells(1) + lat.species_cells(2)
+    assert ob["nonfinite"] == 0
