@@ -11,7 +11,7 @@
 // (c_x = -1) with two scalar loads.  Both cells share the row's table, its
 // references and its index arithmetic.  The second cell of the last pair
 // of an odd row lies in the row padding: it is computed from in-bounds
-// values and never stored or summed.
+// values and stored there (nothing reads it), never summed.
 //
 // The arithmetic is that of step_body (moments, interface friction from
 // lagged velocities, trapezoidal electron-phonon friction and sinks, Guo
@@ -41,7 +41,6 @@ template <> struct Pair<float> {
     __device__ static float2 load2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
     __device__ static float load1(const float *p) { return __ldg(p); }
     __device__ static void store2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
-    __device__ static void store1(float *p, float v) { *p = v; }
 };
 template <> struct Pair<__half> {
     __device__ static float2 load2(const __half *p)
@@ -50,7 +49,6 @@ template <> struct Pair<__half> {
     }
     __device__ static float load1(const __half *p) { return Storage<__half>::load(p); }
     __device__ static void store2(__half *p, float2 v) { *reinterpret_cast<unsigned *>(p) = f32x2_to_f16x2_sat(v); }
-    __device__ static void store1(__half *p, float v) { Storage<__half>::store(p, v); }
 };
 template <> struct Pair<__nv_bfloat16> {
     __device__ static float2 load2(const __nv_bfloat16 *p)
@@ -62,7 +60,6 @@ template <> struct Pair<__nv_bfloat16> {
     {
         *reinterpret_cast<unsigned *>(p) = f32x2_to_bf16x2_sat(v);
     }
-    __device__ static void store1(__nv_bfloat16 *p, float v) { Storage<__nv_bfloat16>::store(p, v); }
 };
 
 struct Cell2 {
@@ -319,33 +316,24 @@ __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const floa
     }
 }
 
-// Store g* of both cells (only the first when the second is padding),
-// encoded against the row's references for 16-bit storage:
-// (g - ref) * scale = fma(g, scale, -ref * scale) exactly, scale being a
-// power of two.
+// Store g* of both cells, encoded against the row's references for 16-bit
+// storage: (g - ref) * scale = fma(g, scale, -ref * scale) exactly, scale
+// being a power of two.  The second cell of an odd row's last pair goes to
+// the row padding, which nothing reads (one store per direction, no
+// predicated pair).
 template <int Q, typename S>
 __device__ __forceinline__ void store_pair(const float2 g[Q], S *__restrict__ out, int row_stride,
-                                           int base, bool both, const float *enc, float scale)
+                                           int base, const float *enc, float scale)
 {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float2 v = g[i];
         if constexpr (Storage<S>::kRef) v = fma2(v, b2(scale), b2(-__ldg(enc + i) * scale));
-        S *q = out + (long long)i * row_stride + base;
-        if (both)
-            Pair<S>::store2(q, v);
-        else
-            Pair<S>::store1(q, v.x);
+        Pair<S>::store2(out + (long long)i * row_stride + base, v);
     }
 }
 
-__device__ __forceinline__ void store_u2(float *q, float2 v, bool both)
-{
-    if (both)
-        *reinterpret_cast<float2 *>(q) = v;
-    else
-        *q = v.x;
-}
+__device__ __forceinline__ void store_u2(float *q, float2 v) { *reinterpret_cast<float2 *>(q) = v; }
 
 // x-sums over the 32-wide segments of a warp whose threads hold CPT cells
 // each (32 / CPT threads per segment) of NV per-thread values (the sums of
@@ -435,7 +423,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
         water_math2<Q>(p, p.U1[kFluid], p.U2[kFluid], p.U1[kSolid], p.U2[kSolid], R, X.x0, g, c, j);
         if (q5.y >= 0 && live) {
             const int ns = p.n_slots[kFluid];
-            for (int a = 0; a < 3; ++a) store_u2(p.U0[kFluid] + (a * ns + q5.y) * nxp + X.x0, c.u[a], both);
+            for (int a = 0; a < 3; ++a) store_u2(p.U0[kFluid] + (a * ns + q5.y) * nxp + X.x0, c.u[a]);
         }
         collide2<Q>(g, c, j, p.rho0, p.om[0]);
         if constexpr (NOISE) {
@@ -444,7 +432,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
             if (both) thermal_noise<Q, float>(p, cell + 1, [&](int i, float v) { g[i].y += v; });
         }
         if (live)
-            store_pair<Q, S>(g, static_cast<S *>(p.out[0]), p.n_rows[kFluid] * nxp, row * nxp + X.x0, both,
+            store_pair<Q, S>(g, static_cast<S *>(p.out[0]), p.n_rows[kFluid] * nxp, row * nxp + X.x0,
                              ref_row<float, S>(p.enc_out[0], row), sc);
         if constexpr (ACC) {
             float acc[2 * Q];
@@ -468,15 +456,14 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     if (q5.y >= 0 && live) {
         const int ns = p.n_slots[kSolid];
         for (int a = 0; a < 3; ++a) {
-            store_u2(p.U0[kSolid] + (a * ns + q5.y) * nxp + X.x0, ce.u[a], both);
-            store_u2(p.U0[kSolid] + ((a + 3) * ns + q5.y) * nxp + X.x0, cp.u[a], both);
+            store_u2(p.U0[kSolid] + (a * ns + q5.y) * nxp + X.x0, ce.u[a]);
+            store_u2(p.U0[kSolid] + ((a + 3) * ns + q5.y) * nxp + X.x0, cp.u[a]);
         }
     }
     const int stride = p.n_rows[kSolid] * nxp, base = row * nxp + X.x0;
     collide2<Q>(ge, ce, je, p.rho0, p.om[1]);
     if (live)
-        store_pair<Q, S>(ge, static_cast<S *>(p.out[1]), stride, base, both,
-                         ref_row<float, S>(p.enc_out[1], row), sc);
+        store_pair<Q, S>(ge, static_cast<S *>(p.out[1]), stride, base, ref_row<float, S>(p.enc_out[1], row), sc);
     float acc[ACC ? 2 * Q : 1];
     if constexpr (ACC) {
 #pragma unroll
@@ -486,8 +473,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
                     ref_row<float, S>(p.dec_in[2], row), inv, gp);
     collide2<Q>(gp, cp, jp, p.rho0, p.om[2], p.q_p);
     if (live)
-        store_pair<Q, S>(gp, static_cast<S *>(p.out[2]), stride, base, both,
-                         ref_row<float, S>(p.enc_out[2], row), sc);
+        store_pair<Q, S>(gp, static_cast<S *>(p.out[2]), stride, base, ref_row<float, S>(p.enc_out[2], row), sc);
     if constexpr (ACC) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) acc[Q + i] = (live ? gp[i].x : 0.f) + (both ? gp[i].y : 0.f);
