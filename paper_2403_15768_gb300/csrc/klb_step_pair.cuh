@@ -15,14 +15,12 @@
 //
 // The arithmetic is that of step_body (moments, interface friction from
 // lagged velocities, trapezoidal electron-phonon friction and sinks, Guo
-// velocity, BGK + Guo collision with the FP32 moment fix-up).  The collision
-// uses that the equilibrium and Guo terms together are a quadratic form in
-// c_i: with fo = 1 - om/2,
-//   om (geq_i - w_i rho0) + fo F_i = w_i (a + b.c_i + c_i.M c_i),
-//   a = om (drho - 1.5 rho u.u) - 3 fo u.F,   b = 3 om rho u + 3 fo F,
-//   M = 4.5 (om rho u u^T + fo (u F^T + F u^T)),
-// so the nine coefficients are formed once per cell and each direction costs
-// a few additions (Eq. 2 with Guo's forcing term).
+// velocity, BGK + Guo collision with the FP32 moment fix-up), with the
+// collision evaluated per pair of opposite directions: for c_ibar = -c_i the
+// equilibrium and forcing terms split into parts even and odd in c,
+//   teq = e0 + 4.5 rho (c.u)^2  +-  3 rho (c.u),
+//   tF  = -3 u.F + 9 (c.u)(c.F) +-  3 (c.F),
+// computed once per pair.
 
 #pragma once
 
@@ -72,6 +70,31 @@ struct Cell2 {
 struct Cols {
     int x0, pm_a, pp_a, pp_b;
 };
+
+template <int Q>
+__host__ __device__ constexpr int opp(int i)
+{
+    return dir_index<Q>(-cx<Q>(i), -cy<Q>(i), -cz<Q>(i));
+}
+
+// c_i . v for a pair of cells.
+template <int Q>
+__device__ __forceinline__ float2 cdot2(int i, const float2 v[3])
+{
+    const int c[3] = {cx<Q>(i), cy<Q>(i), cz<Q>(i)};
+    float2 r = b2(0.f);
+    bool any = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] == 0) continue;
+        if (!any)
+            r = c[a] > 0 ? v[a] : make_float2(-v[a].x, -v[a].y);
+        else
+            r = c[a] > 0 ? add2(r, v[a]) : sub2(r, v[a]);
+        any = true;
+    }
+    return r;
+}
 
 // Mass and momentum of a population set, summed through the pairs of
 // opposite directions (s = g_i + g_ibar, d = g_i - g_ibar) in shallow trees,
@@ -227,75 +250,40 @@ __device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const floa
     }
 }
 
-// BGK + Guo collision of both cells from the quadratic form above, then the
-// FP32 fix-up of mass and momentum (see collide; q as there: 1 for the
-// second-order equilibrium, 0 for the linear one of phonons as damped waves,
-// which scales the u-quadratic part of a and all of M).  The coefficients
-// carry the edge weight w_e (a_e = w_e a, b_e = w_e b, m_aa = w_e M_aa,
-// m_ab = 2 w_e M_ab); a rest or axis direction scales them by its weight
-// ratio.  With P_a = 9 w_e (om rho u_a / 2 + fo F_a): m_aa = u_a P_a and
-// m_ab = u_a P_b + u_b P_a.  g is left holding g*.
+// BGK + Guo collision of both cells, per pair of opposite directions, then
+// the FP32 fix-up of mass and momentum (see collide; q as there: 1 for the
+// second-order equilibrium, 0 for the linear one of phonons as damped
+// waves).  g is left holding g*.
 template <int Q, bool FIX = true>
 __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const float2 j[3], float rho0,
                                          float om, float q = 1.f)
 {
-    constexpr int D = Q == 19 ? 3 : 2;
-    constexpr int kEdge = dir_index<Q>(1, 1, 0);
-    constexpr float we = float(wt<Q>(kEdge));
-    constexpr float W0 = float(wt<Q>(0) / wt<Q>(kEdge));                       // rest / edge weight
-    constexpr float WA = float(wt<Q>(dir_index<Q>(1, 0, 0)) / wt<Q>(kEdge));  // axis / edge weight
-    const float om1 = 1.f - om, fo = 1.f - 0.5f * om;
     const float2 rho = add2(b2(rho0), c.drho);
-    float2 uu = mul2(c.u[0], c.u[0]), uF = mul2(c.u[0], c.F[0]);
-#pragma unroll
-    for (int a = 1; a < D; ++a) {
-        uu = fma2(c.u[a], c.u[a], uu);
-        uF = fma2(c.u[a], c.F[a], uF);
-    }
+    const float2 uu = fma2(c.u[2], c.u[2], fma2(c.u[1], c.u[1], mul2(c.u[0], c.u[0])));
+    const float2 uF = fma2(c.u[2], c.F[2], fma2(c.u[1], c.F[1], mul2(c.u[0], c.F[0])));
     const float2 e0 = fma2(mul2(b2(-1.5f * q), rho), uu, c.drho);
-    const float2 ae = fma2(b2(om * we), e0, mul2(b2(-3.f * q * fo * we), uF));
-    const float2 r3 = mul2(b2(3.f * om * we), rho);
-    const float2 r45 = mul2(b2(4.5f * q * om * we), rho);
-    float2 be[D], P[D], md[D], mo[3];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        be[a] = fma2(r3, c.u[a], mul2(b2(3.f * fo * we), c.F[a]));
-        P[a] = fma2(r45, c.u[a], mul2(b2(9.f * q * fo * we), c.F[a]));
-        md[a] = mul2(c.u[a], P[a]);
+    const float2 r45 = mul2(b2(4.5f * q), rho);
+    const float2 m3uF = mul2(b2(-3.f * q), uF);
+    const float om1 = 1.f - om, fo = 1.f - 0.5f * om;
+    {
+        const float w = float(wt<Q>(0));
+        g[0] = fma2(b2(om1), g[0], fma2(b2(om * w), e0, mul2(b2(fo * w), m3uF)));
     }
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = a + 1; b < D; ++b) mo[a + b - 1] = fma2(c.u[a], P[b], mul2(c.u[b], P[a]));
-    g[0] = fma2(b2(om1), g[0], mul2(b2(W0), ae));
-    const float2 aA = mul2(b2(WA), ae);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-        // +-e_a: WA (a_e + m_aa +- b_a)
-        const int ip = dir_index<Q>(a == 0, a == 1, a == 2);
-        const int im = dir_index<Q>(-(a == 0), -(a == 1), -(a == 2));
-        const float2 E = fma2(b2(WA), md[a], aA), O = mul2(b2(WA), be[a]);
-        g[ip] = fma2(b2(om1), g[ip], add2(E, O));
-        g[im] = fma2(b2(om1), g[im], sub2(E, O));
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-#pragma unroll
-        for (int b = a + 1; b < D; ++b) {
-            // s_a e_a + s_b e_b: a_e + m_aa + m_bb + s_a s_b m_ab + s_a b_a + s_b b_b
-            const int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
-            const int ipp = dir_index<Q>(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
-            const int imm = dir_index<Q>(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]);
-            const int ipm = dir_index<Q>(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
-            const int imp = dir_index<Q>(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]);
-            const float2 base = add2(add2(ae, md[a]), md[b]);
-            const float2 Ep = add2(base, mo[a + b - 1]), Em = sub2(base, mo[a + b - 1]);
-            const float2 Op = add2(be[a], be[b]), Om = sub2(be[a], be[b]);
-            g[ipp] = fma2(b2(om1), g[ipp], add2(Ep, Op));
-            g[imm] = fma2(b2(om1), g[imm], sub2(Ep, Op));
-            g[ipm] = fma2(b2(om1), g[ipm], add2(Em, Om));
-            g[imp] = fma2(b2(om1), g[imp], sub2(Em, Om));
-        }
+    for (int i = 1; i < Q; ++i) {
+        if (opp<Q>(i) < i) continue;
+        const int ib = opp<Q>(i);
+        const float w = float(wt<Q>(i));
+        const float2 cu = cdot2<Q>(i, c.u);
+        const float2 cF = cdot2<Q>(i, c.F);
+        // even parts: e0 + 4.5 rho cu^2 and -3 u.F + 9 cu cF
+        const float2 se = fma2(r45, mul2(cu, cu), e0);
+        const float2 sf = fma2(b2(9.f * q), mul2(cu, cF), m3uF);
+        const float2 S = fma2(b2(om * w), se, mul2(b2(fo * w), sf));
+        // odd parts: 3 rho cu and 3 cF
+        const float2 A = fma2(mul2(b2(3.f * om * w), rho), cu, mul2(b2(3.f * fo * w), cF));
+        g[i] = fma2(b2(om1), g[i], add2(S, A));
+        g[ib] = fma2(b2(om1), g[ib], sub2(S, A));
     }
     if constexpr (!FIX) return;
     float2 m, pm[3];
