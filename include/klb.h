@@ -337,8 +337,11 @@ klb_status klb_set_state(klb_lattice *lat, const double *g, const double *U1,
  * generation and refresh) repeats after 6 steps, or 384 with 16-bit storage,
  * so one table of per-lattice kernel arguments per phase of that period
  * describes every step.  The
- * tables live in the caller's device buffer (klb_batch_bytes); a whole
- * period is captured once in a CUDA graph and replayed.  The batch enqueues
+ * tables live in the caller's device buffer (klb_batch_bytes), with a count
+ * of the periods completed since they were built (the step number each
+ * replayed step needs: FP32 storage draws the dither of its fix-up from the
+ * cell and the step); a whole period is captured once in a CUDA graph and
+ * replayed.  The batch enqueues
  * its work on a stream of its own, ordered after and before the members'
  * stream with events.  Members stay usable on their own between batch calls
  * (observables, fields, state); stepping a member alone takes it out of phase

@@ -858,7 +858,7 @@ struct klb_batch {
     int period = 6;
     int width = kBlockX;
     int nblocks = 0;
-    size_t args_size = 0, table_off = 0, prefix_off = 0;
+    size_t args_size = 0, table_off = 0, prefix_off = 0, reps_off = 0;
     std::vector<StepPlan> plans;  // per (phase, member)
     std::vector<char> acc;        // per phase: some member accumulates x-sums
     std::vector<int64_t> base_step;  // members' steps at phase 0
@@ -886,12 +886,14 @@ int batch_period(int storage) { return reduced_storage(storage) ? 6 * 2 * kRefEv
 
 size_t args_size(int storage) { return storage == KLB_FP64 ? sizeof(StepArgs<double>) : sizeof(StepArgs<float>); }
 
-size_t batch_layout(int n, int storage, size_t *table_off, size_t *prefix_off)
+// Batch buffer: argument tables [phase][member], block prefix, period count.
+size_t batch_layout(int n, int storage, size_t *table_off, size_t *prefix_off, size_t *reps_off)
 {
     const size_t tb = (size_t)batch_period(storage) * n * args_size(storage);
     *table_off = 0;
     *prefix_off = (tb + 255) / 256 * 256;
-    return *prefix_off + ((size_t)(n + 1) * sizeof(int) + 255) / 256 * 256;
+    *reps_off = *prefix_off + ((size_t)(n + 1) * sizeof(int) + 255) / 256 * 256;
+    return *reps_off + 256;
 }
 
 void destroy_graph(klb_batch *B)
@@ -922,13 +924,18 @@ klb_status build_tables(klb_batch *B, int width)
             B->plans[(size_t)k * n + m] = sp;
             B->acc[k] |= (char)sp.acc;
             char *slot = host.data() + ((size_t)k * n + m) * B->args_size;
+            const uint32_t *reps = (const uint32_t *)(B->base + B->reps_off);
             if (B->storage == KLB_FP64) {
                 StepArgs<double> a;
                 fill_args_at(L, st, width, a);
+                a.step_reps = reps;
+                a.step_period = P;
                 std::memcpy(slot, &a, sizeof a);
             } else {
                 StepArgs<float> a;
                 fill_args_at(L, st, width, a);
+                a.step_reps = reps;
+                a.step_period = P;
                 if (reduced(L))
                     for (int s = 0; s < 3; ++s) a.enc_out[s] = (const float *)dev(L, L->plan.ref_enc[sp.outgen][s]);
                 std::memcpy(slot, &a, sizeof a);
@@ -944,6 +951,7 @@ klb_status build_tables(klb_batch *B, int width)
     KLB_BCUDA(B, cudaMemcpy(B->base + B->table_off, host.data(), host.size(), cudaMemcpyHostToDevice));
     KLB_BCUDA(B, cudaMemcpy(B->base + B->prefix_off, prefix.data(), prefix.size() * sizeof(int),
                             cudaMemcpyHostToDevice));
+    KLB_BCUDA(B, cudaMemset(B->base + B->reps_off, 0, sizeof(uint32_t)));
     B->width = width;
     B->nblocks = prefix[n];
     B->phase = 0;
@@ -973,8 +981,10 @@ cudaError_t launch_phase(klb_batch *B, int k)
         if (e != cudaSuccess) return e;
     }
     const char *table = B->base + B->table_off + (size_t)k * n * B->args_size;
-    return launch_batch(B->Q, B->storage, table, (const int *)(B->base + B->prefix_off), (int)n,
-                        B->nblocks, B->width, B->acc[k] != 0, B->stream);
+    cudaError_t e = launch_batch(B->Q, B->storage, table, (const int *)(B->base + B->prefix_off), (int)n,
+                                 B->nblocks, B->width, B->acc[k] != 0, B->stream);
+    if (e == cudaSuccess && k == B->period - 1) e = launch_count_period((uint32_t *)(B->base + B->reps_off), B->stream);
+    return e;
 }
 
 klb_status capture_graph(klb_batch *B)
@@ -1060,8 +1070,8 @@ klb_status run_steps(klb_batch *B, int64_t nsteps, bool use_graph)
 
 size_t klb::batch_table_bytes(int storage, int n)
 {
-    size_t t, p;
-    return n < 1 ? 0 : batch_layout(n, storage, &t, &p);
+    size_t t, p, r;
+    return n < 1 ? 0 : batch_layout(n, storage, &t, &p, &r);
 }
 
 extern "C" {
@@ -1069,8 +1079,8 @@ extern "C" {
 size_t klb_batch_bytes(klb_lattice *const *members, int n)
 {
     if (!members || n < 1 || !members[0]) return 0;
-    size_t t, p;
-    return batch_layout(n, members[0]->desc.storage, &t, &p);
+    size_t t, p, r;
+    return batch_layout(n, members[0]->desc.storage, &t, &p, &r);
 }
 
 klb_status klb_batch_create(klb_lattice *const *members, int n, void *dev_buf, size_t bytes,
@@ -1098,7 +1108,7 @@ klb_status klb_batch_create(klb_lattice *const *members, int n, void *dev_buf, s
     B->storage = members[0]->desc.storage;
     B->period = batch_period(B->storage);
     B->args_size = args_size(B->storage);
-    const size_t need = batch_layout(n, B->storage, &B->table_off, &B->prefix_off);
+    const size_t need = batch_layout(n, B->storage, &B->table_off, &B->prefix_off, &B->reps_off);
     if (!dev_buf || ((uintptr_t)dev_buf & 255u)) {
         delete B;
         return fail(nullptr, KLB_EINVAL, "dev_buf must be a 256-byte aligned device pointer");

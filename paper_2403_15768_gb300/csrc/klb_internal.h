@@ -161,6 +161,11 @@ struct alignas(16) StepArgs {
     T noise_amp;           // sqrt(3 rho0 kT omega (2 - omega))
     uint32_t key[2];       // generator key (seed)
     uint32_t step_lo, step_hi;  // the step being taken
+    // batches: the record is of a period's phase, replayed; the step taken is
+    // step_lo + *step_reps * step_period (low 32 bits), step_reps counting the
+    // periods completed since the tables were built (null for one lattice)
+    const uint32_t *step_reps;
+    int step_period;
     unsigned *bounds_err;  // debug builds: first out-of-range index site
 };
 
@@ -181,6 +186,8 @@ cudaError_t launch(int Q, int storage, const void *args, int mode, int nblocks, 
 cudaError_t launch_ref(int Q, int storage, const void *args, float *const enc[3],
                        float *const dec[3], cudaStream_t s);
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s);
+// One more period completed by a batch (StepArgs::step_reps).
+cudaError_t launch_count_period(uint32_t *reps, cudaStream_t s);
 // One step of many lattices in one launch: table[l] holds the arguments of
 // lattice l, prefix[l] its first block (prefix[n] = total blocks).
 cudaError_t launch_batch(int Q, int storage, const void *table, const int *prefix, int n,

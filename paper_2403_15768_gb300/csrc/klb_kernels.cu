@@ -68,6 +68,17 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const double *__r
     if (threadIdx.x == 0) sums[k] = red[0];
 }
 
+// Periods completed by a batch since its tables were built: one launch at
+// the end of every period, in stream order after the period's last step
+// (the next step kernel reads the count after its dependency wait).
+__global__ void k_count_period(uint32_t *reps) { *reps += 1u; }
+
+cudaError_t launch_count_period(uint32_t *reps, cudaStream_t s)
+{
+    k_count_period<<<1, 1, 0, s>>>(reps);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const double *partials, int nblocks, double *sums, cudaStream_t s)
 {
     k_finalize<<<kNumSums, kFinalizeThreads, 0, s>>>(partials, nblocks, sums);

@@ -250,13 +250,67 @@ __device__ __forceinline__ void solid_math2(const StepArgs<float> &p, const floa
     }
 }
 
+// Unbiased rounding of the FP32 fix-up (FP32 storage).  The fix-up's
+// increments are mostly below half an ulp of the populations they go to
+// (about 1e-10 against |g| ~ 2e-3), so round-to-nearest drops them, and in
+// a steady state it drops them the same way in every step: a per-row bias
+// of the stored momentum that the slowest shear mode accumulates (velocity
+// error ~4e-6 after 10^4 steps on the benchmark pipe).  Here each increment
+// is added with a uniform dither of one ulp of the target, a + RN(b + d),
+// d in [-ulp/2, ulp/2): the rounded sum is a + b on average (subtractive-free
+// dither), and the dither changes from row to row and step to step.  The
+// bits come from the lowbias32 integer hash (C. Wellons) of the row's
+// cross-section cell, the species and the step: every cell of a row gets
+// the same dither, so that a state that does not vary along x stays so
+// (and a lattice reproduces its x-slices), while the bias, which a
+// steady state repeats step after step, becomes noise in time.
+__device__ __forceinline__ uint32_t lowbias32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Uniform in [-1/2, 1/2) from the top 23 bits of r.
+__device__ __forceinline__ float dither_unit(uint32_t r) { return __int_as_float(0x3f800000u | (r >> 9)) - 1.5f; }
+
+// One ulp of a normal a (exponent field times 2^-23; 0 for zero or a subnormal).
+__device__ __forceinline__ float ulp_of(float a)
+{
+    return __int_as_float(__float_as_int(a) & 0x7f800000) * 1.1920928955078125e-7f;
+}
+
+// a + b with a one-ulp dither (r: random bits; the same dither fraction for
+// both cells, each scaled by its own ulp).
+__device__ __forceinline__ float2 add2_dither(float2 a, float2 b, uint32_t r)
+{
+    const float u = dither_unit(r);
+    return add2(a, add2(b, make_float2(u * ulp_of(a.x), u * ulp_of(a.y))));
+}
+
+// Dither seed of the row with cross-section cell cs for species s at step n.
+__device__ __forceinline__ uint32_t dither_seed(uint32_t cs, uint32_t n, int s)
+{
+    return lowbias32(cs ^ lowbias32(n * 3u + (uint32_t)s));
+}
+
 // BGK + Guo collision of both cells, per pair of opposite directions, then
 // the FP32 fix-up of mass and momentum (see collide; q as there: 1 for the
 // second-order equilibrium, 0 for the linear one of phonons as damped
 // waves).  g is left holding g*.
-template <int Q, bool FIX = true>
+//
+// DITHER (FP32 storage): the residuals of the fix-up are summed from the
+// per-direction differences g_i - g*_i, which are small, so that they are
+// exact to about 1e-12 (the sums Sum g_i and Sum g*_i of the plain fix-up
+// each round at the scale of |g|), and the increments are added with
+// add2_dither (seed sd: dither_seed).  16-bit storage rounds the stored
+// differences to nearest anyway and keeps the plain fix-up.
+template <int Q, bool FIX = true, bool DITHER = false>
 __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const float2 j[3], float rho0,
-                                         float om, float q = 1.f)
+                                         float om, float q = 1.f, uint32_t sd = 0u)
 {
     const float2 rho = add2(b2(rho0), c.drho);
     const float2 uu = fma2(c.u[2], c.u[2], fma2(c.u[1], c.u[1], mul2(c.u[0], c.u[0])));
@@ -265,9 +319,13 @@ __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const floa
     const float2 r45 = mul2(b2(4.5f * q), rho);
     const float2 m3uF = mul2(b2(-3.f * q), uF);
     const float om1 = 1.f - om, fo = 1.f - 0.5f * om;
+    constexpr bool DIFF = FIX && DITHER;
+    float2 dm = b2(0.f), dj[3] = {b2(0.f), b2(0.f), b2(0.f)};  // Sum (g - g*), Sum c (g - g*)
     {
         const float w = float(wt<Q>(0));
+        const float2 g0 = g[0];
         g[0] = fma2(b2(om1), g[0], fma2(b2(om * w), e0, mul2(b2(fo * w), m3uF)));
+        if constexpr (DIFF) dm = sub2(g0, g[0]);
     }
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -282,10 +340,36 @@ __device__ __forceinline__ void collide2(float2 g[Q], const Cell2 &c, const floa
         const float2 S = fma2(b2(om * w), se, mul2(b2(fo * w), sf));
         // odd parts: 3 rho cu and 3 cF
         const float2 A = fma2(mul2(b2(3.f * om * w), rho), cu, mul2(b2(3.f * fo * w), cF));
-        g[i] = fma2(b2(om1), g[i], add2(S, A));
-        g[ib] = fma2(b2(om1), g[ib], sub2(S, A));
+        const float2 gi = g[i], gb = g[ib];
+        g[i] = fma2(b2(om1), gi, add2(S, A));
+        g[ib] = fma2(b2(om1), gb, sub2(S, A));
+        if constexpr (DIFF) {
+            const float2 di = sub2(gi, g[i]), db = sub2(gb, g[ib]);
+            dm = add2(dm, add2(di, db));
+            const float2 dd = sub2(di, db);
+            const int cc[3] = {cx<Q>(i), cy<Q>(i), cz<Q>(i)};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (cc[k] > 0) dj[k] = add2(dj[k], dd);
+                if (cc[k] < 0) dj[k] = sub2(dj[k], dd);
+            }
+        }
     }
     if constexpr (!FIX) return;
+    if constexpr (DIFF) {
+        // Sum g*_final = Sum g and Sum c g*_final = Sum c g + F
+        g[0] = add2_dither(g[0], dm, sd);
+#pragma unroll
+        for (int k = 0; k < (Q == 19 ? 3 : 2); ++k) {
+            const float2 h = mul2(b2(0.5f), add2(dj[k], c.F[k]));
+            const int ip = dir_index<Q>(k == 0, k == 1, k == 2);
+            const int im = dir_index<Q>(-(k == 0), -(k == 1), -(k == 2));
+            const uint32_t mp = 0x9E3779B9u * (uint32_t)(2 * k + 1) | 1u, mm = 0x9E3779B9u * (uint32_t)(2 * k + 2) | 1u;
+            g[ip] = add2_dither(g[ip], h, sd * mp);
+            g[im] = add2_dither(g[im], make_float2(-h.x, -h.y), sd * mm);
+        }
+        return;
+    }
     float2 m, pm[3];
     moments2<Q>(g, m, pm);
     const float2 px = pm[0], py = pm[1];
@@ -401,7 +485,9 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     const bool xbounce = (q7.x & kXBounce) != 0;
 
     const int seg = ACC ? thread_segment<2>(p, water, row, x_first) : -1;
-    pdl_wait();  // populations, lagged velocities and references below
+    pdl_wait();  // populations, lagged velocities, references and the period count below
+    constexpr bool DITHER = !Storage<S>::kRef;
+    const uint32_t n_step = p.step_lo + (p.step_reps ? *p.step_reps * (uint32_t)p.step_period : 0u);
 
     if (water) {
         float2 g[Q], j[3];
@@ -413,7 +499,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
             const int ns = p.n_slots[kFluid];
             for (int a = 0; a < 3; ++a) store_u2(p.U0[kFluid] + (a * ns + q5.y) * nxp + X.x0, c.u[a]);
         }
-        collide2<Q>(g, c, j, p.rho0, p.om[0]);
+        collide2<Q, true, DITHER>(g, c, j, p.rho0, p.om[0], 1.f, dither_seed((uint32_t)q7.y, n_step, 0));
         if constexpr (NOISE) {
             const uint32_t cell = (uint32_t)X.x0 + (uint32_t)p.nx * (uint32_t)q7.y;
             thermal_noise<Q, float>(p, cell, [&](int i, float v) { g[i].x += v; });
@@ -449,7 +535,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
         }
     }
     const int stride = p.n_rows[kSolid] * nxp, base = row * nxp + X.x0;
-    collide2<Q>(ge, ce, je, p.rho0, p.om[1]);
+    collide2<Q, true, DITHER>(ge, ce, je, p.rho0, p.om[1], 1.f, dither_seed((uint32_t)q7.y, n_step, 1));
     if (live)
         store_pair<Q, S>(ge, static_cast<S *>(p.out[1]), stride, base, ref_row<float, S>(p.enc_out[1], row), sc);
     float acc[ACC ? 2 * Q : 1];
@@ -459,7 +545,7 @@ __device__ __forceinline__ void step_body2(const StepArgs<float> &p, int b)
     }
     pull_row2<Q, S>(static_cast<const S *>(p.in[2]), src, xm, xp, xbounce, X,
                     ref_row<float, S>(p.dec_in[2], row), inv, gp);
-    collide2<Q>(gp, cp, jp, p.rho0, p.om[2], p.q_p);
+    collide2<Q, true, DITHER>(gp, cp, jp, p.rho0, p.om[2], p.q_p, dither_seed((uint32_t)q7.y, n_step, 2));
     if (live)
         store_pair<Q, S>(gp, static_cast<S *>(p.out[2]), stride, base, ref_row<float, S>(p.enc_out[2], row), sc);
     if constexpr (ACC) {

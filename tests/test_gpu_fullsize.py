@@ -10,10 +10,12 @@ against the oracle.
 
 Bars: FP32 velocity fields within 1e-5 relative L2 after 10^4 steps and the
 slip length within 0.1%; flow rate and slip length within 1% for 16-bit
-storage.  The other tolerances (16-bit velocity fields, the sweep and the
+storage.  FP32 storage is held to 1e-6 (measured 0.9e-7-1.7e-7 since its
+fix-up rounds its increments without bias; the unbiased rounding lost
+would show as a few 1e-6).  The other tolerances (16-bit velocity fields, the sweep and the
 served requests after 300 steps) are the errors measured on GB300 with a
 margin of about 2x: sweep fields and flow rates of six members FP32 at most
-2.9e-6, FP16 at most 6.0e-4 (a narrow slab whose flow is still small, so
+1.7e-7 (held to the FP32 1e-6), FP16 at most 6.0e-4 (a narrow slab whose flow is still small, so
 that the 16-bit rounding is a larger fraction of it; the 1% bar for 16-bit
 storage is far off); the served requests, retired at the same step count,
 at the sweep's bounds.
@@ -88,7 +90,7 @@ def test_large_nanotube_16bit_against_oracle_and_fp32(storage, tol):
     d16 = [rel_l2(u16[s][:, m[s]], u32[s][:, m[s]]) for s in range(3)]
     report = {"fp32": e32, storage: e16, "vs fp32": d16}
     print(report)
-    assert max(e32) <= 1e-5 and max(e16) <= tol and max(d16) <= tol, report
+    assert max(e32) <= 1e-6 and max(e16) <= tol and max(d16) <= tol, report
     assert ob32["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
     assert ob16["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-2)
     for ob in (ob32, ob16):
@@ -96,7 +98,7 @@ def test_large_nanotube_16bit_against_oracle_and_fp32(storage, tol):
         assert ob["nonfinite"] == 0
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 6e-6), ("fp16", 1.5e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("fp16", 1.5e-3)])
 def test_full_sweep_batch_sampled_members_against_oracle(storage, tol):
     """All 96 channels of the sweep in one batch (the benchmark's lattices),
     from rest; six members spanning the size range checked plane by plane."""

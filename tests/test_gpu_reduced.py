@@ -4,7 +4,10 @@ full-size nanotube against the oracle.
 
 Bars: the FP32 velocity field within 1e-5 relative L2 after 10^4 steps and
 the slip length within 0.1%; flow rate and slip length within 1% for 16-bit
-storage.  Where no bar is stated (16-bit velocity fields, the small cases),
+storage.  FP32 storage is held to 1e-6, ten times tighter: its fix-up adds
+its increments with a dither of one ulp (unbiased rounding), which brought
+the measured error from 3.6e-6-4.0e-6 to 0.9e-7-1.7e-7 on the full nanotube
+and the subcase, and a bias coming back would show as a few 1e-6.  Where no bar is stated (16-bit velocity fields, the small cases),
 tolerances are the errors measured on GB300 with a margin of about 2x
 (small pipe after 10^4 steps: FP16 4.6e-6, BF16 2.5e-5; perturbed start
 after 2000 steps: FP16 4.2e-4, BF16 2.6e-3).
@@ -106,7 +109,7 @@ def _per_observable(ob, ob_o):
     return err
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16", 1e-5), ("bf16", 1e-5)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("fp16", 1e-5), ("bf16", 1e-5)])
 def test_full_nanotube_10k_steps_against_oracle(storage, tol):
     """The 512x128x128 nanotube in the benchmark's launch configuration, 10^4
     steps from rest, against the oracle: FP32 velocity fields within 1e-5
@@ -161,7 +164,7 @@ def _sub_oracle():
 XVAR_TOL = {"fp32": 3e-4, "fp16": 4e-3, "bf16": 0.2}
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 1e-5), ("fp16", 2e-5), ("bf16", 2e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-6), ("fp16", 2e-5), ("bf16", 2e-3)])
 def test_subcase_perturbed_start_against_oracle(storage, tol):
     """The 128x64x64 nanotube subcase (radius 24, shell 3) from a seeded,
     x-varying perturbed start, 5000 steps, against the FP64 oracle: velocity
