@@ -102,9 +102,9 @@ def test_d3q19_fp32_pipe_10k_steps_against_fp64_oracle():
     f = o.observe()
     drho, u = lat.get_field()
     masks = species_masks(o.geo, w.nx)
-    for s in range(3):
-        m = masks[s]
-        assert rel_l2(u[s][:, m], f["u"][s][:, m]) <= 1e-5, s
+    errs = [rel_l2(u[s][:, masks[s]], f["u"][s][:, masks[s]]) for s in range(3)]
+    print("pipe r8 fp32 10k rel-L2", errs)
+    assert max(errs) <= 1e-5, errs
     ob_o = observables_from_fields(o.geo, w.nx, w.rho0, f)
     ob_g = lat.observables()
     assert ob_g["slip_length"] == pytest.approx(ob_o["slip_length"], rel=1e-3)
